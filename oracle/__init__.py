@@ -1,0 +1,260 @@
+"""FP64 CPU oracle for the LBE (MRT, D3Q19) and DUGKS steps of Wang, Wang & Guo,
+"Comparison of the LBE and DUGKS methods for DNS of decaying homogeneous
+isotropic turbulence" (arXiv:1601.03815).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The product library
+(``paper_1601_03815_gb300``) never imports it, and it never imports the product.
+
+The time steppers live in ``kin_oracle.c`` (plain C, FP64, OpenMP); this module
+marshals numpy arrays into it and adds the energy spectrum of Eq. 27, computed
+with numpy's FFT as a library step.
+
+Array layout: f has shape (19, nz, ny, nx) (x fastest), u has shape
+(3, nz, ny, nx).  Population order is :func:`lattice`.
+
+Parity status: see the header of ``kin_oracle.h``.  ``spectrum`` is pinned by
+single-mode closed forms and Parseval (tests/test_oracle_stats.py).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kin_oracle.c")
+_SO = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+Q = 19
+
+
+def build(force: bool = False) -> str:
+    """Compile kin_oracle.c into liboracle.so beside it (gcc, -O2, OpenMP)."""
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= max(os.path.getmtime(_SRC),
+                                             os.path.getmtime(os.path.join(_HERE, "kin_oracle.h")))):
+        return _SO
+    tmp = _SO + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_SO)
+            d = ctypes.c_double
+            i = ctypes.c_int
+            p = ctypes.c_void_p
+            lib.orc_lattice.argtypes = [p, p]
+            lib.orc_feq.argtypes = [d, d, d, d, p]
+            lib.orc_moments.argtypes = [p, p, p]
+            lib.orc_mrt_matrix.argtypes = [p]
+            lib.orc_mrt_meq.argtypes = [d, d, d, d, p]
+            lib.orc_mrt_rates.argtypes = [d, p]
+            lib.orc_mrt_collide.argtypes = [p, p, p, p]
+            lib.orc_lbe_step.argtypes = [i, i, i, p, p, p]
+            lib.orc_lbe_step.restype = i
+            lib.orc_dugks_tau.argtypes = [d]
+            lib.orc_dugks_tau.restype = d
+            lib.orc_dugks_prestep_cell.argtypes = [d, d, p, p, p]
+            lib.orc_dugks_step.argtypes = [i, i, i, d, d, p, p]
+            lib.orc_dugks_step.restype = i
+            lib.orc_equilibrium_field.argtypes = [i, i, i, p, p, p]
+            lib.orc_macro.argtypes = [i, i, i, p, p, p]
+            lib.orc_energy_dissipation.argtypes = [i, i, i, d, p, p, p]
+            lib.orc_num_threads.restype = i
+            lib.orc_set_num_threads.argtypes = [i]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return _load().orc_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    _load().orc_set_num_threads(int(n))
+
+
+def lattice():
+    """D3Q19 velocities xi (19, 3) int and weights W (19,) (Sec. II.A)."""
+    xi = np.zeros(Q * 3, dtype=np.int32)
+    w = np.zeros(Q, dtype=np.float64)
+    _load().orc_lattice(_ptr(xi), _ptr(w))
+    return xi.reshape(Q, 3).astype(np.int64), w
+
+
+def feq(drho: float, u) -> np.ndarray:
+    """Discrete equilibrium of Eq. 7 for one cell."""
+    out = np.zeros(Q)
+    _load().orc_feq(float(drho), float(u[0]), float(u[1]), float(u[2]), _ptr(out))
+    return out
+
+
+def moments(f) -> tuple[float, np.ndarray]:
+    f = _f64(f)
+    r = np.zeros(1)
+    j = np.zeros(3)
+    _load().orc_moments(_ptr(f), _ptr(r), _ptr(j))
+    return float(r[0]), j
+
+
+def mrt_matrix() -> np.ndarray:
+    M = np.zeros(Q * Q)
+    _load().orc_mrt_matrix(_ptr(M))
+    return M.reshape(Q, Q)
+
+
+def mrt_meq(drho: float, j) -> np.ndarray:
+    out = np.zeros(Q)
+    _load().orc_mrt_meq(float(drho), float(j[0]), float(j[1]), float(j[2]), _ptr(out))
+    return out
+
+
+def mrt_rates(nu: float) -> np.ndarray:
+    s = np.zeros(Q)
+    _load().orc_mrt_rates(float(nu), _ptr(s))
+    return s
+
+
+def mrt_collide(s, f, meq) -> np.ndarray:
+    s, f, meq = _f64(s), _f64(f), _f64(meq)
+    out = np.zeros(Q)
+    _load().orc_mrt_collide(_ptr(s), _ptr(f), _ptr(meq), _ptr(out))
+    return out
+
+
+def _dims(f: np.ndarray):
+    if f.ndim != 4 or f.shape[0] != Q:
+        raise ValueError("f must have shape (19, nz, ny, nx)")
+    nz, ny, nx = f.shape[1:]
+    return nx, ny, nz
+
+
+def lbe_step(f, nu: float | None = None, s=None) -> np.ndarray:
+    """One MRT-LBE step (Eq. 21) with the Sec. IV.A rates for viscosity nu, or
+    with an explicit rate vector s."""
+    f = _f64(f)
+    nx, ny, nz = _dims(f)
+    if s is None:
+        s = mrt_rates(nu)
+    s = _f64(s)
+    out = np.empty_like(f)
+    rc = _load().orc_lbe_step(nx, ny, nz, _ptr(s), _ptr(f), _ptr(out))
+    if rc != 0:
+        raise RuntimeError("orc_lbe_step failed: %d" % rc)
+    return out
+
+
+def dugks_tau(nu: float) -> float:
+    return _load().orc_dugks_tau(float(nu))
+
+
+def dugks_prestep_cell(tau: float, dt: float, ft):
+    ft = _f64(ft)
+    b = np.zeros(Q)
+    p = np.zeros(Q)
+    _load().orc_dugks_prestep_cell(float(tau), float(dt), _ptr(ft), _ptr(b), _ptr(p))
+    return b, p
+
+
+def dugks_step(f, nu: float, dt: float) -> np.ndarray:
+    """One DUGKS step (Eqs. 9-20) on the stored f-tilde."""
+    f = _f64(f)
+    nx, ny, nz = _dims(f)
+    out = np.empty_like(f)
+    rc = _load().orc_dugks_step(nx, ny, nz, float(nu), float(dt), _ptr(f), _ptr(out))
+    if rc != 0:
+        raise RuntimeError("orc_dugks_step failed: %d" % rc)
+    return out
+
+
+def step(scheme: str, f, nu: float, dt: float) -> np.ndarray:
+    if scheme == "lbe":
+        return lbe_step(f, nu)
+    if scheme == "dugks":
+        return dugks_step(f, nu, dt)
+    raise ValueError(scheme)
+
+
+def equilibrium_field(u, drho=None) -> np.ndarray:
+    """f = f_eq(drho, u) everywhere (Eq. 7); u has shape (3, nz, ny, nx)."""
+    u = _f64(u)
+    nz, ny, nx = u.shape[1:]
+    f = np.empty((Q, nz, ny, nx))
+    d = None if drho is None else _f64(drho)
+    _load().orc_equilibrium_field(nx, ny, nz, None if d is None else _ptr(d), _ptr(u), _ptr(f))
+    return f
+
+
+def macro(f):
+    """delta-rho (nz, ny, nx) and u (3, nz, ny, nx) from f (Eq. 8)."""
+    f = _f64(f)
+    nx, ny, nz = _dims(f)
+    drho = np.empty((nz, ny, nx))
+    u = np.empty((3, nz, ny, nx))
+    _load().orc_macro(nx, ny, nz, _ptr(f), _ptr(drho), _ptr(u))
+    return drho, u
+
+
+def energy_dissipation(u, nu: float):
+    """E = <u.u>/2 and eps = 2 nu <s_ab s_ab> (central differences)."""
+    u = _f64(u)
+    nz, ny, nx = u.shape[1:]
+    E = np.zeros(1)
+    eps = np.zeros(1)
+    _load().orc_energy_dissipation(nx, ny, nz, float(nu), _ptr(u), _ptr(E), _ptr(eps))
+    return float(E[0]), float(eps[0])
+
+
+def stats(f, nu: float):
+    """(E, eps) of the state f."""
+    _, u = macro(f)
+    return energy_dissipation(u, nu)
+
+
+def spectrum(u, nshell: int | None = None):
+    """Energy spectrum of Eq. 27 summed over integer shells.
+
+    u_hat(k) = N^-3 sum_x u(x) exp(-i k.x); mode n goes to shell
+    floor(|n| + 1/2); E(s) = sum over the shell of |u_hat|^2 / 2.  Returns
+    (E[0..nshell-1], Omega) where Omega = sum over all modes of
+    |k|^2 |u_hat|^2 / 2 with k = 2 pi n / N, so eps_spectral = 2 nu Omega
+    (Eq. 26).  The default nshell covers every mode (shells up to sqrt(3) N/2).
+    """
+    u = _f64(u)
+    nz, ny, nx = u.shape[1:]
+    ncell = nx * ny * nz
+    uh = np.fft.fftn(u, axes=(1, 2, 3)) / ncell
+    e = 0.5 * np.sum(np.abs(uh) ** 2, axis=0)
+    kz = np.fft.fftfreq(nz, 1.0 / nz)
+    ky = np.fft.fftfreq(ny, 1.0 / ny)
+    kx = np.fft.fftfreq(nx, 1.0 / nx)
+    n2 = kz[:, None, None] ** 2 + ky[None, :, None] ** 2 + kx[None, None, :] ** 2
+    shell = np.floor(np.sqrt(n2) + 0.5).astype(np.int64)
+    if nshell is None:
+        nshell = int(shell.max()) + 1
+    E = np.bincount(shell.ravel(), weights=e.ravel(), minlength=nshell)[:nshell]
+    k2 = (2 * np.pi) ** 2 * (kz[:, None, None] ** 2 / nz ** 2 + ky[None, :, None] ** 2 / ny ** 2
+                             + kx[None, None, :] ** 2 / nx ** 2)
+    omega = float(np.sum(k2 * e))
+    return E, omega
