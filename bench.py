@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Benchmark of the LBE and DUGKS time steps on GB300 (one JSON line on stdout).
+
+Workload (per GPU): decaying homogeneous isotropic turbulence on a periodic
+256^3 box, D3Q19, FP32 storage, seeded initial field with k0 = 8, Ma = 0.15,
+Re_lambda = 70 (viscosity from the field).  One bench step advances an MRT-LBE
+simulation by one step (dt = 1) and a DUGKS simulation by one step (dt = 0.5);
+E and eps of both are read back every 10 steps and E(k) every 200 steps (the
+logging cadence of the 128^3 run).  value = cell updates of all ranks / the
+slowest rank's time, in MLUPS.  The state (2 x 1.27 GB per scheme) is far
+larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (a smaller box from the same recipe) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LBE/DUGKS MLUPS at 256^3 FP32, % HBM roofline; ensemble p50/p99 latency"
+BYTES_PER_CELL = {"f32": 152, "f16": 76, "bf16": 76, "f64": 304}  # 19 loads + 19 stores
+K0, MA, RE_LAMBDA = 8.0, 0.15, 70.0
+STATS_EVERY, SPECTRUM_EVERY = 10, 200
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=400)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--N", type=int, default=256)
+    p.add_argument("--storage", choices=["f32", "f16", "bf16", "f64"], default="f32")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while the
+    timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline_sample(seconds_target: float = 15.0):
+    """Time the FP64 oracle (as it stands) on a 128^3 box of the same recipe:
+    one LBE and one DUGKS step, repeated while under the time budget."""
+    import kin_inputs as ki
+    import oracle
+
+    oracle.build()
+    n = 128
+    u, info = ki.dhit_velocity(n, 1300, K0, MA, return_info=True)
+    nu = ki.nu_from_re_lambda(info["u_prime"], info["omega"], RE_LAMBDA)
+    f = oracle.equilibrium_field(u)
+    g = f
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        g = oracle.lbe_step(f, nu)
+        g = oracle.dugks_step(f, nu, 0.5)
+        reps += 1
+        if time.perf_counter() - t0 > seconds_target / 2 or reps >= 4:
+            break
+    dt = time.perf_counter() - t0
+    del g
+    return {"value": 2 * reps * n ** 3 / dt / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "%d x (one MRT-LBE + one DUGKS step) on a %d^3 box of the same recipe "
+                      "(k0=8, Ma=0.15), FP64, %.1f s" % (reps, n, dt)}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import kin_inputs as ki
+    import oracle
+
+    oracle.build()
+    # size the per-step sample so W + K steps take about two minutes
+    probe_n = 24
+    u, info = ki.dhit_velocity(probe_n, 1300, min(K0, probe_n / 4), MA, return_info=True)
+    f = oracle.equilibrium_field(u)
+    t0 = time.perf_counter()
+    oracle.lbe_step(f, 0.01)
+    oracle.dugks_step(f, 0.01, 0.5)
+    per_cell = (time.perf_counter() - t0) / probe_n ** 3
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    n = int((budget / per_cell) ** (1.0 / 3.0)) // 2 * 2
+    n = max(16, min(128, n))
+    u, info = ki.dhit_velocity(n, 1300, min(K0, n / 4), MA, return_info=True)
+    nu = ki.nu_from_re_lambda(info["u_prime"], info["omega"], RE_LAMBDA)
+    fl = oracle.equilibrium_field(u)
+    fd = fl.copy()
+    for _ in range(args.warmup):
+        fl = oracle.lbe_step(fl, nu)
+        fd = oracle.dugks_step(fd, nu, 0.5)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        fl = oracle.lbe_step(fl, nu)
+        fd = oracle.dugks_step(fd, nu, 0.5)
+    elapsed = time.perf_counter() - t0
+    value = 2 * args.steps * n ** 3 / elapsed / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * elapsed / max(1, args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "DHIT D3Q19, one MRT-LBE + one DUGKS step per bench step, "
+                               "k0=8, Ma=0.15, Re_lambda=70; oracle sample box %d^3" % n,
+                   "N": n, "storage": "f64"},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": "%d^3 box of the 256^3 recipe per step, %d steps" % (n, args.steps)},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1601_03815_gb300 as kin
+
+    world, rank, local = _dist()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    kin.load()
+    st = {"f32": kin.F32, "f16": kin.F16, "bf16": kin.BF16, "f64": kin.F64}[args.storage]
+    N = args.N
+    stream = torch.cuda.Stream()
+    seed = 1300 + rank
+    lbe = kin.Sim(N, kin.LBE_MRT, 0.01, MA, 1.0, st, stream=stream)
+    dug = kin.Sim(N, kin.DUGKS, 0.01, MA, 0.5, st, stream=stream)
+    lbe.init_field(seed, K0, RE_LAMBDA)
+    dug.init_field(seed, K0, RE_LAMBDA)
+
+    def bench_step(k, record=None):
+        if record is not None:
+            record[0].record(stream)
+        lbe.step(1)
+        if record is not None:
+            record[1].record(stream)
+        dug.step(1)
+        if record is not None:
+            record[2].record(stream)
+        if (k + 1) % STATS_EVERY == 0:
+            spec = (k + 1) % SPECTRUM_EVERY == 0
+            lbe.stats(spectrum=spec)
+            dug.stats(spectrum=spec)
+
+    for k in range(args.warmup):
+        bench_step(k)
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = lbe.kernel_launches + dug.kernel_launches
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    start.record(stream)
+    for k in range(args.steps):
+        bench_step(k, evs[k])
+    stop.record(stream)
+    torch.cuda.synchronize()
+    clocks.stop()
+    launches = lbe.kernel_launches + dug.kernel_launches - launches0
+    elapsed = start.elapsed_time(stop) / 1000.0
+    t_lbe = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps / 1000.0
+    t_dug = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps / 1000.0
+    tmax = elapsed
+    if dist:
+        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tmax = float(t.item())
+        dist.barrier()
+    cells = N ** 3
+    value = world * 2 * cells * args.steps / tmax / 1e6
+
+    # end to end through the C ABI: the initial field from pinned host memory,
+    # then per step one step of each scheme and a read-back of E and eps
+    e2e = None
+    if not args.no_e2e:
+        import kin_inputs as ki
+
+        u0 = ki.dhit_velocity(N, seed, K0, MA)
+        pinned = torch.empty(u0.shape, dtype=torch.float64, pin_memory=True)
+        pinned.numpy()[...] = u0
+        hu = pinned.numpy()
+        k_e2e = max(10, min(args.steps, 200))
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lbe.set_velocity(hu)
+        dug.set_velocity(hu)
+        for k in range(k_e2e):
+            lbe.step(1)
+            dug.step(1)
+            lbe.stats()
+            dug.stats()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([te], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * 2 * cells * k_e2e / te / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": int(2 * u0.nbytes / k_e2e), "d2h_bytes_per_step": 2 * 2 * 8,
+               "steps": k_e2e,
+               "what": "kin_set_velocity from pinned host memory for both schemes, then per step "
+                       "kin_step(1) and kin_stats(E, eps) of each; host wall clock"}
+
+    peak, peak_kind = _peaks()
+    bpc = BYTES_PER_CELL[args.storage]
+    per = {}
+    for name, t, sim in [("lbe", t_lbe, lbe), ("dugks", t_dug, dug)]:
+        gbs = bpc * cells / t / 1e9
+        per[name] = {"mlups": cells / t / 1e6, "ms_per_step": 1000 * t, "gbs": gbs,
+                     "frac_of_%s_hbm" % peak_kind: gbs / peak, "launches_per_step": sim.step_launches}
+    dom = "dugks" if t_dug >= t_lbe else "lbe"
+    t_dom = t_dug if dom == "dugks" else t_lbe
+    achieved = bpc * cells / t_dom / 1e9
+    traffic = None
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tmax / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
+        "data": "synthetic",
+        "config": {"workload": "DHIT %d^3 D3Q19: one MRT-LBE step (dt=1) + one DUGKS step (dt=0.5) "
+                               "per bench step; k0=8, Ma=0.15, Re_lambda=70; E, eps every %d steps, "
+                               "E(k) every %d" % (N, STATS_EVERY, SPECTRUM_EVERY),
+                   "N": N, "storage": args.storage,
+                   "l2": "inputs larger than L2 (one copy of f is %.2f GB), no flush"
+                         % (cells * bpc / 2 / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "per_scheme": per,
+        "roofline": {"bound": "hbm", "kernel": "%s step" % dom, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic,
+                     "algorithmic_bytes_per_launch": bpc * cells},
+        "clocks": clocks.summary(),
+        "gpu_launches": launches * world,
+        "e2e": e2e,
+    }
+    for sim in (lbe, dug):
+        sim.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample()
+    elif rank == 0:
+        line["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,154 @@
+/*
+ * libkin: GB300 (sm_103a) CUDA library for the per-time-step update of the
+ * D3Q19 distributions of decaying homogeneous isotropic turbulence on a
+ * periodic N^3 box, with the two schemes compared by Wang, Wang & Guo,
+ * "Comparison of the LBE and DUGKS methods for DNS of decaying homogeneous
+ * isotropic turbulence" (arXiv:1601.03815):
+ *   KIN_LBE_MRT  MRT lattice Boltzmann collide-and-stream, Sec. II.B, Eq. 21
+ *   KIN_DUGKS    discrete unified gas-kinetic scheme, Sec. II.A, Eqs. 9-20
+ *
+ * Units: lattice units, dx = 1, c = 1, RT = c_s^2 = 1/3, rho0 = 1.
+ *
+ * Host array layouts (all FP64, owned by the caller, never retained):
+ *   distributions  f[i][z][y][x], x fastest, 19 * N^3 doubles; population i
+ *                  has velocity kin_lattice()[i]; f_i is the deviation from
+ *                  W_i rho0 (Eq. 7 carries no rest part).  For KIN_LBE_MRT
+ *                  this is the pre-collision f at t_n (left side of Eq. 21 at
+ *                  t_n); for KIN_DUGKS it is the cell-averaged f-tilde at t_n
+ *                  (Eq. 9).
+ *   velocity       u[c][z][y][x], c = x, y, z, 3 * N^3 doubles.
+ *
+ * Every int-returning call returns KIN_OK (0) or a negative KIN_E* code;
+ * kin_strerror() names the code and kin_last_error() describes the last
+ * failure on the calling thread.  No call retains a host pointer.  All device
+ * work is ordered on the simulation's stream; calls that return host data
+ * synchronise that stream first.
+ */
+#ifndef KIN_H
+#define KIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kin_sim kin_sim;
+
+enum kin_scheme { KIN_LBE_MRT = 0, KIN_DUGKS = 1 };
+
+/* Storage precision of f in device memory.  KIN_F32/F16/BF16 compute in FP32;
+ * KIN_F64 stores and computes in FP64.  Reductions (E, eps, spectrum) always
+ * accumulate in FP64. */
+enum kin_storage { KIN_F32 = 0, KIN_F16 = 1, KIN_BF16 = 2, KIN_F64 = 3 };
+
+enum kin_status {
+    KIN_OK = 0,
+    KIN_EINVAL = -1,     /* bad argument (size, scheme, dt, NULL pointer) */
+    KIN_ENOMEM = -2,     /* device allocation failed */
+    KIN_ECUDA = -3,      /* a CUDA / cuFFT call failed */
+    KIN_ENONFINITE = -4, /* the state holds NaN/Inf (the run blew up) */
+    KIN_ETIMEOUT = -5,   /* a bounded device-side wait gave up */
+    KIN_ESTATE = -6      /* call not valid in the current state */
+};
+
+/* D3Q19 velocity set (Sec. II.A, Eq. 5) in the population order used by every
+ * array of this library: xi[3*i + a], i = 0..18, and weights w[19]. */
+int kin_lattice(int* xi, double* w);
+
+/* Bytes of device memory a simulation of this size holds after kin_create
+ * (state buffers only; statistics add 3*N^3 doubles on first use, the
+ * spectrum a further 3*N^2*(N/2+1) complex doubles). */
+size_t kin_footprint_bytes(int N, int scheme, int storage);
+
+/* Create a simulation on the current CUDA device.
+ *   N        box edge, 2 <= N <= 1024
+ *   scheme   KIN_LBE_MRT or KIN_DUGKS
+ *   nu       kinematic viscosity (> 0).  LBE: s9 = s13 = 1/(3 nu + 1/2)
+ *            (Sec. IV.A, Eq. 23).  DUGKS: tau = nu / RT.
+ *   Ma       target Mach number u'/c_s used by kin_init_field (> 0)
+ *   dt       time step.  LBE: must be 1 (dt = dx).  DUGKS: 0 < dt <= 1/sqrt(2)
+ *            (CFL number gamma = sqrt(2) dt <= 1, Sec. IV.A).
+ *   storage  enum kin_storage
+ *   stream   cudaStream_t to run on, or NULL for a stream the library owns
+ *   out      receives the handle; the state starts at rest (f = 0)
+ * Errors: KIN_EINVAL, KIN_ENOMEM, KIN_ECUDA. */
+int kin_create(int N, int scheme, double nu, double Ma, double dt, int storage, void* stream,
+               kin_sim** out);
+
+/* Seeded initial field of Sec. III, Eq. 25 (solenoidal Gaussian field with
+ * E(k) = k^4 exp(-2 k^2 / k0^2) on integer shells 1..N/2-1, rescaled so that
+ * u' = Ma c_s, Eq. 29), then f = f_eq(0, u0) (Eq. 7).  Random numbers come from
+ * the splitmix64 stream described in kin_inputs.  If re_lambda > 0 the
+ * viscosity is reset so that the field has Taylor-microscale Reynolds number
+ * re_lambda (Eqs. 26, 28, 30: nu = u'^2 sqrt(15 / (2 Omega)) / Re_lambda,
+ * Omega = sum |k|^2 E(k)); otherwise nu is kept.  Resets time to 0.
+ * Requires even N >= 4.  Synchronous. */
+int kin_init_field(kin_sim* sim, uint64_t seed, double k0, double re_lambda);
+
+/* f = f_eq(0, u) everywhere (Eq. 7) from a host velocity field [3][N^3].
+ * Resets time to 0.  Synchronous. */
+int kin_set_velocity(kin_sim* sim, const double* u);
+
+/* Load / read the state in the canonical host layout (see top of file).
+ * Synchronous. kin_set_f resets time to 0. */
+int kin_set_f(kin_sim* sim, const double* f);
+int kin_get_f(kin_sim* sim, double* f);
+
+/* Canonical f at n cells (linear indices x + N (y + N z)) into out[n][19].
+ * Synchronous. */
+int kin_sample_f(kin_sim* sim, const int64_t* cells, int64_t n, double* out);
+
+/* Velocity field u[3][N^3] (host) of the current state (Eq. 8 / Eq. 12).
+ * Synchronous. */
+int kin_get_velocity(kin_sim* sim, double* u);
+
+/* Enqueue n >= 0 time steps on the simulation's stream and return. */
+int kin_step(kin_sim* sim, int n);
+
+/* Statistics of the current state (synchronises the stream):
+ *   E    = <u.u>/2, the kinetic energy per unit mass (Eq. 26 via Parseval)
+ *   eps  = 2 nu <s_ab s_ab>, s_ab from periodic second-order central
+ *          differences of u (grid form of Eq. 26)
+ *   Ek   NULL, or kin_num_shells(N) doubles: E(s) = sum over modes with
+ *          floor(|n| + 1/2) = s of |u_hat|^2 / 2, u_hat = N^-3 FFT(u) (Eq. 27)
+ * Any output pointer may be NULL.  FP64 reductions in a fixed order: the
+ * result is bitwise reproducible for a given state.
+ * Returns KIN_ENONFINITE if E is not finite. */
+int kin_stats(kin_sim* sim, double* E, double* eps, double* Ek);
+
+/* Number of spectrum shells for edge N: 1 + floor(sqrt(3) (N/2) + 1/2). */
+int kin_num_shells(int N);
+
+/* Number of kernel launches one kin_step(sim, 1) enqueues. */
+int kin_step_launches(const kin_sim* sim);
+
+/* Total launches of this library's own kernels for sim since kin_create
+ * (cuFFT's kernels are not counted). */
+int64_t kin_kernel_launches(const kin_sim* sim);
+
+/* Block until the simulation's stream is idle. */
+int kin_sync(kin_sim* sim);
+
+double kin_get_nu(const kin_sim* sim);
+double kin_get_dt(const kin_sim* sim);
+double kin_get_time(const kin_sim* sim);  /* steps taken * dt */
+int64_t kin_get_step(const kin_sim* sim); /* steps taken since the last reset */
+int kin_get_N(const kin_sim* sim);
+int kin_get_scheme(const kin_sim* sim);
+int kin_get_storage(const kin_sim* sim);
+
+/* Human-readable name of a status code; never NULL. */
+const char* kin_strerror(int code);
+
+/* Description of the last failure on the calling thread ("" if none). */
+const char* kin_last_error(void);
+
+/* Release all device memory of sim; NULL-safe. */
+void kin_destroy(kin_sim* sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KIN_H */

@@ -1,0 +1,253 @@
+"""Python binding of libkin, the GB300 (sm_103a) CUDA library for the LBE and
+DUGKS time steps of decaying homogeneous isotropic turbulence
+(Wang, Wang & Guo, arXiv:1601.03815).
+
+This module only marshals arguments to the C ABI declared in include/kin.h;
+every step of the solver runs in the library's CUDA kernels.  There is no CPU
+fallback: if libkin.so cannot be built or loaded, ``load()`` raises.
+
+Host arrays are numpy FP64: f has shape (19, N, N, N) indexed [i][z][y][x],
+u has shape (3, N, N, N).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+LBE_MRT = 0
+DUGKS = 1
+F32, F16, BF16, F64 = 0, 1, 2, 3
+STORAGE_NAMES = {F32: "f32", F16: "f16", BF16: "bf16", F64: "f64"}
+SCHEME_NAMES = {LBE_MRT: "lbe", DUGKS: "dugks"}
+
+KIN_OK = 0
+KIN_EINVAL = -1
+KIN_ENOMEM = -2
+KIN_ECUDA = -3
+KIN_ENONFINITE = -4
+KIN_ETIMEOUT = -5
+KIN_ESTATE = -6
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libkin.so")
+_lib = None
+_lock = threading.Lock()
+
+
+class KinError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str):
+        super().__init__("%s failed: %s (%d): %s" % (where, _strerror(code), code, detail))
+        self.code = code
+
+
+def _strerror(code: int) -> str:
+    if _lib is None:
+        return str(code)
+    return _lib.kin_strerror(code).decode()
+
+
+def _declare(lib):
+    c_int, c_double, c_void_p, c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+    c_i64, c_u64 = ctypes.c_int64, ctypes.c_uint64
+    P = ctypes.c_void_p
+    sig = {
+        "kin_lattice": (c_int, [P, P]),
+        "kin_footprint_bytes": (c_size_t, [c_int, c_int, c_int]),
+        "kin_create": (c_int, [c_int, c_int, c_double, c_double, c_double, c_int, c_void_p, P]),
+        "kin_init_field": (c_int, [P, c_u64, c_double, c_double]),
+        "kin_set_velocity": (c_int, [P, P]),
+        "kin_set_f": (c_int, [P, P]),
+        "kin_get_f": (c_int, [P, P]),
+        "kin_sample_f": (c_int, [P, P, c_i64, P]),
+        "kin_get_velocity": (c_int, [P, P]),
+        "kin_step": (c_int, [P, c_int]),
+        "kin_stats": (c_int, [P, P, P, P]),
+        "kin_num_shells": (c_int, [c_int]),
+        "kin_sync": (c_int, [P]),
+        "kin_step_launches": (c_int, [P]),
+        "kin_kernel_launches": (c_i64, [P]),
+        "kin_get_nu": (c_double, [P]),
+        "kin_get_dt": (c_double, [P]),
+        "kin_get_time": (c_double, [P]),
+        "kin_get_step": (c_i64, [P]),
+        "kin_get_N": (c_int, [P]),
+        "kin_get_scheme": (c_int, [P]),
+        "kin_get_storage": (c_int, [P]),
+        "kin_strerror": (ctypes.c_char_p, [c_int]),
+        "kin_last_error": (ctypes.c_char_p, []),
+        "kin_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+def load(build_if_needed: bool = True):
+    """Load libkin.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import build as _build
+
+        if build_if_needed and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libkin.so not found at %s; run paper_1601_03815_gb300.build" % LIB_PATH)
+        _lib = _declare(ctypes.CDLL(LIB_PATH, mode=ctypes.RTLD_GLOBAL))
+        return _lib
+
+
+def lib():
+    return _lib if _lib is not None else load()
+
+
+def _check(rc: int, where: str):
+    if rc != KIN_OK:
+        raise KinError(rc, where, lib().kin_last_error().decode())
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def lattice():
+    """D3Q19 velocities (19, 3) and weights (19,) in the library's order."""
+    xi = np.zeros(57, dtype=np.int32)
+    w = np.zeros(19, dtype=np.float64)
+    _check(lib().kin_lattice(_ptr(xi), _ptr(w)), "kin_lattice")
+    return xi.reshape(19, 3).astype(np.int64), w
+
+
+def footprint_bytes(N: int, scheme: int, storage: int) -> int:
+    return int(lib().kin_footprint_bytes(N, scheme, storage))
+
+
+def num_shells(N: int) -> int:
+    return int(lib().kin_num_shells(N))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream"))
+
+
+class Sim:
+    """One simulation (state resident in device memory)."""
+
+    def __init__(self, N: int, scheme: int, nu: float, Ma: float = 0.1, dt: float | None = None,
+                 storage: int = F32, stream=None):
+        if dt is None:
+            dt = 1.0 if scheme == LBE_MRT else 0.5
+        h = ctypes.c_void_p()
+        _check(lib().kin_create(int(N), int(scheme), float(nu), float(Ma), float(dt), int(storage),
+                                _stream_handle(stream), ctypes.byref(h)), "kin_create")
+        self._h = h
+        self.N = int(N)
+        self.scheme = int(scheme)
+        self.storage = int(storage)
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().kin_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- state
+    def init_field(self, seed: int, k0: float, re_lambda: float = 0.0):
+        _check(lib().kin_init_field(self._h, ctypes.c_uint64(seed), float(k0), float(re_lambda)),
+               "kin_init_field")
+
+    def set_velocity(self, u: np.ndarray):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        if u.shape != (3, self.N, self.N, self.N):
+            raise ValueError("u must have shape (3, N, N, N)")
+        _check(lib().kin_set_velocity(self._h, _ptr(u)), "kin_set_velocity")
+
+    def set_f(self, f: np.ndarray):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        if f.shape != (19, self.N, self.N, self.N):
+            raise ValueError("f must have shape (19, N, N, N)")
+        _check(lib().kin_set_f(self._h, _ptr(f)), "kin_set_f")
+
+    def get_f(self) -> np.ndarray:
+        f = np.empty((19, self.N, self.N, self.N))
+        _check(lib().kin_get_f(self._h, _ptr(f)), "kin_get_f")
+        return f
+
+    def sample_f(self, cells) -> np.ndarray:
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        out = np.empty((cells.size, 19))
+        _check(lib().kin_sample_f(self._h, _ptr(cells), cells.size, _ptr(out)), "kin_sample_f")
+        return out
+
+    def get_velocity(self) -> np.ndarray:
+        u = np.empty((3, self.N, self.N, self.N))
+        _check(lib().kin_get_velocity(self._h, _ptr(u)), "kin_get_velocity")
+        return u
+
+    # -- time stepping and statistics
+    def step(self, n: int = 1):
+        _check(lib().kin_step(self._h, int(n)), "kin_step")
+
+    def stats(self, spectrum: bool = False):
+        """(E, eps) or (E, eps, Ek) of the current state."""
+        E = np.zeros(1)
+        eps = np.zeros(1)
+        Ek = np.zeros(num_shells(self.N)) if spectrum else None
+        _check(lib().kin_stats(self._h, _ptr(E), _ptr(eps), None if Ek is None else _ptr(Ek)),
+               "kin_stats")
+        if spectrum:
+            return float(E[0]), float(eps[0]), Ek
+        return float(E[0]), float(eps[0])
+
+    @property
+    def step_launches(self) -> int:
+        return int(lib().kin_step_launches(self._h))
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(lib().kin_kernel_launches(self._h))
+
+    def sync(self):
+        _check(lib().kin_sync(self._h), "kin_sync")
+
+    @property
+    def nu(self) -> float:
+        return lib().kin_get_nu(self._h)
+
+    @property
+    def dt(self) -> float:
+        return lib().kin_get_dt(self._h)
+
+    @property
+    def time(self) -> float:
+        return lib().kin_get_time(self._h)
+
+    @property
+    def steps_taken(self) -> int:
+        return int(lib().kin_get_step(self._h))

@@ -1,0 +1,451 @@
+// C ABI of libkin (declared in include/kin.h).
+#include "kin.h"
+#include "kin_common.cuh"
+#include "kin_init.h"
+#include "kin_internal.h"
+
+#include <cufft.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+using namespace kin;
+
+struct kin_sim {
+    int N = 0, scheme = 0, storage = 0;
+    double nu = 0, Ma = 0, dt = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    void* fbp = nullptr;  // DUGKS f-bar-plus scratch
+    int64_t step = 0;
+    // statistics scratch (lazy)
+    double* u = nullptr;      // 3 N^3
+    double2* uh = nullptr;    // 3 N^2 (N/2+1)
+    double* red = nullptr;    // block partials
+    double* red_out = nullptr;
+    size_t red_cap = 0;
+    cufftHandle d2z = 0, z2d = 0;
+    bool have_d2z = false, have_z2d = false;
+    int block_lbe = 0, block_dugks = 0;
+    int64_t launches = 0;  // own kernel launches
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CK(call)                                                                             \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(e_ == cudaErrorMemoryAllocation ? KIN_ENOMEM : KIN_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                  \
+    } while (0)
+
+#define CKFFT(call)                                                                         \
+    do {                                                                                    \
+        cufftResult r_ = (call);                                                            \
+        if (r_ != CUFFT_SUCCESS)                                                            \
+            return fail(KIN_ECUDA, "%s: cufft error %d (%s:%d)", #call, (int)r_, __FILE__, __LINE__); \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+size_t ncell(const kin_sim* s) { return (size_t)s->N * s->N * s->N; }
+bool shifted(const kin_sim* s) { return s->scheme == KIN_LBE_MRT; }
+size_t state_bytes(const kin_sim* s) { return Q * ncell(s) * storage_bytes(s->storage); }
+
+int ensure_u(kin_sim* s) {
+    if (!s->u) CK(cudaMalloc(&s->u, sizeof(double) * 3 * ncell(s)));
+    const size_t need = 2 * (size_t)std::max(stats_blocks(s->N), spectrum_blocks(s->N)) *
+                        (size_t)std::max(kin_num_shells(s->N), 2);
+    if (s->red_cap < need) {
+        if (s->red) cudaFree(s->red);
+        s->red = nullptr;
+        CK(cudaMalloc(&s->red, sizeof(double) * need));
+        s->red_cap = need;
+    }
+    if (!s->red_out) CK(cudaMalloc(&s->red_out, sizeof(double) * (4 + kin_num_shells(s->N))));
+    return KIN_OK;
+}
+
+int ensure_uh(kin_sim* s) {
+    if (!s->uh) CK(cudaMalloc(&s->uh, sizeof(double2) * 3 * (size_t)s->N * s->N * (s->N / 2 + 1)));
+    return KIN_OK;
+}
+
+size_t nmode(const kin_sim* s) { return (size_t)s->N * s->N * (s->N / 2 + 1); }
+
+int valid(const kin_sim* s) {
+    if (!s) return fail(KIN_EINVAL, "NULL simulation handle");
+    return KIN_OK;
+}
+
+int launch_step(kin_sim* s) {
+    const void* src = s->buf[s->cur];
+    void* dst = s->buf[s->cur ^ 1];
+    cudaError_t e;
+    if (s->scheme == KIN_LBE_MRT)
+        e = lbe_step(s->storage, src, dst, s->N, s->nu, s->block_lbe, s->stream);
+    else
+        e = dugks_step(s->storage, src, dst, s->fbp, s->N, s->nu, s->dt, s->block_dugks, s->stream);
+    if (e != cudaSuccess) return fail(KIN_ECUDA, "step launch: %s", cudaGetErrorString(e));
+    s->launches += kin_step_launches(s);
+    s->cur ^= 1;
+    s->step += 1;
+    return KIN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kin_lattice(int* xi, double* w) {
+    if (!xi || !w) return fail(KIN_EINVAL, "NULL output");
+    for (int i = 0; i < Q; ++i) {
+        xi[3 * i + 0] = cx(i);
+        xi[3 * i + 1] = cy(i);
+        xi[3 * i + 2] = cz(i);
+        w[i] = (double)w36(i) / 36.0;
+    }
+    return KIN_OK;
+}
+
+size_t kin_footprint_bytes(int N, int scheme, int storage) {
+    if (N < 2 || storage < 0 || storage > 3) return 0;
+    const size_t n = (size_t)N * N * N;
+    size_t b = 2 * Q * n * storage_bytes(storage);
+    if (scheme == KIN_DUGKS) b += Q * n * dugks_scratch_bytes(storage);
+    return b;
+}
+
+int kin_num_shells(int N) {
+    if (N < 1) return 0;
+    const long long h = N / 2;
+    const long long m = 3 * h * h;
+    return 1 + (int)std::floor(std::sqrt((double)m) + 0.5);
+}
+
+int kin_create(int N, int scheme, double nu, double Ma, double dt, int storage, void* stream,
+               kin_sim** out) {
+    if (!out) return fail(KIN_EINVAL, "NULL output handle");
+    *out = nullptr;
+    if (N < 2 || N > 1024) return fail(KIN_EINVAL, "N = %d outside [2, 1024]", N);
+    if (scheme != KIN_LBE_MRT && scheme != KIN_DUGKS) return fail(KIN_EINVAL, "unknown scheme %d", scheme);
+    if (storage < KIN_F32 || storage > KIN_F64) return fail(KIN_EINVAL, "unknown storage %d", storage);
+    if (!(nu > 0.0) || !std::isfinite(nu)) return fail(KIN_EINVAL, "nu must be positive, got %g", nu);
+    if (!(Ma > 0.0) || !std::isfinite(Ma)) return fail(KIN_EINVAL, "Ma must be positive, got %g", Ma);
+    if (scheme == KIN_LBE_MRT && std::fabs(dt - 1.0) > 1e-12)
+        return fail(KIN_EINVAL, "LBE requires dt = 1 (dt = dx), got %g", dt);
+    if (scheme == KIN_DUGKS && (!(dt > 0.0) || dt > 1.0 / std::sqrt(2.0) + 1e-12))
+        return fail(KIN_EINVAL, "DUGKS requires 0 < dt <= 1/sqrt(2), got %g", dt);
+
+    kin_sim* s = new kin_sim();
+    s->N = N;
+    s->scheme = scheme;
+    s->storage = storage;
+    s->nu = nu;
+    s->Ma = Ma;
+    s->dt = scheme == KIN_LBE_MRT ? 1.0 : dt;
+    cudaGetDevice(&s->device);
+    auto bail = [&](int code) {
+        kin_destroy(s);
+        return code;
+    };
+    if (stream) {
+        s->stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(fail(KIN_ECUDA, "stream: %s", cudaGetErrorString(e)));
+        s->own_stream = true;
+    }
+    const size_t sb = state_bytes(s);
+    for (int k = 0; k < 2; ++k) {
+        cudaError_t e = cudaMalloc(&s->buf[k], sb);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(KIN_ENOMEM, "state buffer of %zu bytes: %s", sb, cudaGetErrorString(e)));
+        }
+        e = cudaMemsetAsync(s->buf[k], 0, sb, s->stream);
+        if (e != cudaSuccess) return bail(fail(KIN_ECUDA, "memset: %s", cudaGetErrorString(e)));
+    }
+    if (scheme == KIN_DUGKS) {
+        const size_t fb = Q * ncell(s) * dugks_scratch_bytes(storage);
+        cudaError_t e = cudaMalloc(&s->fbp, fb);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(KIN_ENOMEM, "DUGKS scratch of %zu bytes: %s", fb, cudaGetErrorString(e)));
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return bail(fail(KIN_ECUDA, "sync: %s", cudaGetErrorString(e)));
+    *out = s;
+    return KIN_OK;
+}
+
+void kin_destroy(kin_sim* s) {
+    if (!s) return;
+    DeviceGuard g(s->device);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    for (int k = 0; k < 2; ++k)
+        if (s->buf[k]) cudaFree(s->buf[k]);
+    if (s->fbp) cudaFree(s->fbp);
+    if (s->u) cudaFree(s->u);
+    if (s->uh) cudaFree(s->uh);
+    if (s->red) cudaFree(s->red);
+    if (s->red_out) cudaFree(s->red_out);
+    if (s->have_d2z) cufftDestroy(s->d2z);
+    if (s->have_z2d) cufftDestroy(s->z2d);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+int kin_set_velocity(kin_sim* s, const double* u) {
+    if (int r = valid(s)) return r;
+    if (!u) return fail(KIN_EINVAL, "NULL velocity");
+    DeviceGuard g(s->device);
+    if (int r = ensure_u(s)) return r;
+    CK(cudaMemcpyAsync(s->u, u, sizeof(double) * 3 * ncell(s), cudaMemcpyHostToDevice, s->stream));
+    CK(equilibrium_from_velocity(s->storage, s->u, shifted(s), s->N, s->buf[s->cur], s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->step = 0;
+    return KIN_OK;
+}
+
+int kin_init_field(kin_sim* s, uint64_t seed, double k0, double re_lambda) {
+    if (int r = valid(s)) return r;
+    if (s->N < 4 || (s->N & 1)) return fail(KIN_EINVAL, "kin_init_field needs even N >= 4, got %d", s->N);
+    if (!(k0 > 0.0) || !std::isfinite(k0)) return fail(KIN_EINVAL, "k0 must be positive");
+    DeviceGuard g(s->device);
+    if (int r = ensure_u(s)) return r;
+    if (int r = ensure_uh(s)) return r;
+    const int N = s->N;
+    const size_t nm = nmode(s);
+    double2* u0 = s->uh;
+    double2* u1 = s->uh + nm;
+    double2* u2 = s->uh + 2 * nm;
+    CK(generate_modes(N, seed, u0, u1, u2, s->stream));
+    const int nsh = kin_num_shells(N);
+    CK(spectrum_shells(u0, u1, u2, N, nsh, 1.0, 0, s->red, s->red_out, s->stream));
+    std::vector<double> e(nsh);
+    CK(cudaMemcpyAsync(e.data(), s->red_out, sizeof(double) * nsh, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    // shell targets E_t(s) = s^4 exp(-2 s^2 / k0^2), s = 1..N/2-1; global
+    // factor so that <u.u> = 2 sum E = Ma^2 (u' = Ma c_s, c_s^2 = 1/3)
+    const int smax = N / 2 - 1;
+    std::vector<double> scale(nsh, 0.0);
+    double total = 0.0;
+    for (int sh = 1; sh <= smax; ++sh) {
+        const double sd = (double)sh;
+        const double et = sd * sd * sd * sd * std::exp(-2.0 * sd * sd / (k0 * k0));
+        total += et;
+        scale[sh] = e[sh] > 0.0 ? std::sqrt(et / e[sh]) : 0.0;
+    }
+    const double glob = std::sqrt(s->Ma * s->Ma / (2.0 * total));
+    CK(cudaMemcpyAsync(s->red_out, scale.data(), sizeof(double) * nsh, cudaMemcpyHostToDevice, s->stream));
+    CK(scale_modes(N, s->red_out, glob, u0, u1, u2, s->stream));
+    // Omega = (2 pi / N)^2 sum |n|^2 |u_hat|^2 / 2 and <u.u> = 2 sum |u_hat|^2 / 2
+    CK(spectrum_shells(u0, u1, u2, N, nsh, 1.0, 1, s->red, s->red_out, s->stream));
+    CK(cudaMemcpyAsync(e.data(), s->red_out, sizeof(double) * nsh, cudaMemcpyDeviceToHost, s->stream));
+    std::vector<double> e2(nsh);
+    CK(spectrum_shells(u0, u1, u2, N, nsh, 1.0, 0, s->red, s->red_out, s->stream));
+    CK(cudaMemcpyAsync(e2.data(), s->red_out, sizeof(double) * nsh, cudaMemcpyDeviceToHost, s->stream));
+    // u(x) = sum_n u_hat(n) exp(i 2 pi n.x / N): unnormalised inverse transform
+    if (!s->have_z2d) {
+        CKFFT(cufftPlan3d(&s->z2d, N, N, N, CUFFT_Z2D));
+        s->have_z2d = true;
+    }
+    CKFFT(cufftSetStream(s->z2d, s->stream));
+    for (int c = 0; c < 3; ++c)
+        CKFFT(cufftExecZ2D(s->z2d, (cufftDoubleComplex*)(s->uh + c * nm), s->u + c * ncell(s)));
+    CK(equilibrium_from_velocity(s->storage, s->u, shifted(s), N, s->buf[s->cur], s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    double omega = 0.0, uu = 0.0;
+    for (int sh = 0; sh < nsh; ++sh) {
+        omega += e[sh];
+        uu += e2[sh];
+    }
+    omega *= (2.0 * M_PI / N) * (2.0 * M_PI / N);
+    uu *= 2.0;
+    if (re_lambda > 0.0) {
+        const double up2 = uu / 3.0;
+        s->nu = up2 * std::sqrt(15.0 / (2.0 * omega)) / re_lambda;
+    }
+    s->step = 0;
+    return KIN_OK;
+}
+
+int kin_set_f(kin_sim* s, const double* f) {
+    if (int r = valid(s)) return r;
+    if (!f) return fail(KIN_EINVAL, "NULL f");
+    DeviceGuard g(s->device);
+    if (int r = ensure_u(s)) return r;
+    const size_t n = ncell(s);
+    for (int i = 0; i < Q; ++i) {
+        CK(cudaMemcpyAsync(s->u, f + (size_t)i * n, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
+        CK(set_population(s->storage, i, s->u, shifted(s), s->N, s->buf[s->cur], s->stream));
+    }
+    CK(cudaStreamSynchronize(s->stream));
+    s->step = 0;
+    return KIN_OK;
+}
+
+int kin_get_f(kin_sim* s, double* f) {
+    if (int r = valid(s)) return r;
+    if (!f) return fail(KIN_EINVAL, "NULL f");
+    DeviceGuard g(s->device);
+    if (int r = ensure_u(s)) return r;
+    const size_t n = ncell(s);
+    for (int i = 0; i < Q; ++i) {
+        CK(get_population(s->storage, i, s->buf[s->cur], shifted(s), s->N, s->u, s->stream));
+        CK(cudaMemcpyAsync(f + (size_t)i * n, s->u, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+    }
+    return KIN_OK;
+}
+
+int kin_sample_f(kin_sim* s, const int64_t* cells, int64_t n, double* out) {
+    if (int r = valid(s)) return r;
+    if (n < 0 || (n > 0 && (!cells || !out))) return fail(KIN_EINVAL, "bad sample arguments");
+    if (n == 0) return KIN_OK;
+    const int64_t nc = (int64_t)ncell(s);
+    for (int64_t k = 0; k < n; ++k)
+        if (cells[k] < 0 || cells[k] >= nc) return fail(KIN_EINVAL, "cell index %lld out of range", (long long)cells[k]);
+    DeviceGuard g(s->device);
+    int64_t* dc = nullptr;
+    double* dout = nullptr;
+    CK(cudaMalloc(&dc, sizeof(int64_t) * n));
+    cudaError_t e = cudaMalloc(&dout, sizeof(double) * n * Q);
+    if (e != cudaSuccess) {
+        cudaFree(dc);
+        return fail(KIN_ENOMEM, "sample buffer: %s", cudaGetErrorString(e));
+    }
+    int rc = KIN_OK;
+    do {
+        if ((e = cudaMemcpyAsync(dc, cells, sizeof(int64_t) * n, cudaMemcpyHostToDevice, s->stream)) != cudaSuccess) break;
+        if ((e = sample_cells(s->storage, s->buf[s->cur], shifted(s), s->N, dc, n, dout, s->stream)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(out, dout, sizeof(double) * n * Q, cudaMemcpyDeviceToHost, s->stream)) != cudaSuccess) break;
+        e = cudaStreamSynchronize(s->stream);
+    } while (0);
+    if (e != cudaSuccess) rc = fail(KIN_ECUDA, "sample: %s", cudaGetErrorString(e));
+    cudaFree(dc);
+    cudaFree(dout);
+    return rc;
+}
+
+int kin_get_velocity(kin_sim* s, double* u) {
+    if (int r = valid(s)) return r;
+    if (!u) return fail(KIN_EINVAL, "NULL u");
+    DeviceGuard g(s->device);
+    if (int r = ensure_u(s)) return r;
+    CK(velocity_field(s->storage, s->buf[s->cur], shifted(s), s->N, s->u, s->stream));
+    CK(cudaMemcpyAsync(u, s->u, sizeof(double) * 3 * ncell(s), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return KIN_OK;
+}
+
+int kin_step(kin_sim* s, int n) {
+    if (int r = valid(s)) return r;
+    if (n < 0) return fail(KIN_EINVAL, "negative step count");
+    DeviceGuard g(s->device);
+    for (int k = 0; k < n; ++k)
+        if (int r = launch_step(s)) return r;
+    return KIN_OK;
+}
+
+int kin_stats(kin_sim* s, double* E, double* eps, double* Ek) {
+    if (int r = valid(s)) return r;
+    DeviceGuard g(s->device);
+    if (int r = ensure_u(s)) return r;
+    CK(velocity_field(s->storage, s->buf[s->cur], shifted(s), s->N, s->u, s->stream));
+    CK(energy_dissipation(s->u, s->N, s->nu, s->red, s->red_out, s->stream));
+    s->launches += 3;
+    double ed[2];
+    CK(cudaMemcpyAsync(ed, s->red_out, sizeof(ed), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (E) *E = ed[0];
+    if (eps) *eps = ed[1];
+    if (!std::isfinite(ed[0]) || !std::isfinite(ed[1]))
+        return fail(KIN_ENONFINITE, "non-finite statistics at step %lld", (long long)s->step);
+    if (Ek) {
+        if (int r = ensure_uh(s)) return r;
+        const int N = s->N;
+        if (!s->have_d2z) {
+            CKFFT(cufftPlan3d(&s->d2z, N, N, N, CUFFT_D2Z));
+            s->have_d2z = true;
+        }
+        CKFFT(cufftSetStream(s->d2z, s->stream));
+        const size_t nm = nmode(s);
+        for (int c = 0; c < 3; ++c)
+            CKFFT(cufftExecD2Z(s->d2z, s->u + c * ncell(s), (cufftDoubleComplex*)(s->uh + c * nm)));
+        const int nsh = kin_num_shells(N);
+        const double inv = 1.0 / ((double)N * N * N);
+        CK(spectrum_shells(s->uh, s->uh + nm, s->uh + 2 * nm, N, nsh, inv, 0, s->red, s->red_out, s->stream));
+        s->launches += 2;
+        CK(cudaMemcpyAsync(Ek, s->red_out, sizeof(double) * nsh, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+    }
+    return KIN_OK;
+}
+
+int kin_step_launches(const kin_sim* s) {
+    if (!s) return 0;
+    return s->scheme == KIN_LBE_MRT ? 1 : 2;
+}
+
+int64_t kin_kernel_launches(const kin_sim* s) { return s ? s->launches : 0; }
+
+int kin_sync(kin_sim* s) {
+    if (int r = valid(s)) return r;
+    DeviceGuard g(s->device);
+    CK(cudaStreamSynchronize(s->stream));
+    return KIN_OK;
+}
+
+double kin_get_nu(const kin_sim* s) { return s ? s->nu : 0.0; }
+double kin_get_dt(const kin_sim* s) { return s ? s->dt : 0.0; }
+double kin_get_time(const kin_sim* s) { return s ? (double)s->step * s->dt : 0.0; }
+int64_t kin_get_step(const kin_sim* s) { return s ? s->step : 0; }
+int kin_get_N(const kin_sim* s) { return s ? s->N : 0; }
+int kin_get_scheme(const kin_sim* s) { return s ? s->scheme : -1; }
+int kin_get_storage(const kin_sim* s) { return s ? s->storage : -1; }
+
+const char* kin_strerror(int code) {
+    switch (code) {
+        case KIN_OK: return "ok";
+        case KIN_EINVAL: return "invalid argument";
+        case KIN_ENOMEM: return "out of device memory";
+        case KIN_ECUDA: return "CUDA error";
+        case KIN_ENONFINITE: return "non-finite state";
+        case KIN_ETIMEOUT: return "device wait timed out";
+        case KIN_ESTATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+const char* kin_last_error(void) { return g_err; }
+
+}  // extern "C"

@@ -1,0 +1,377 @@
+// Statistics and state conversion kernels.
+//
+//   velocity_kernel        u = sum xi_i f_i (Eq. 8 / Eq. 12), FP64 out
+//   ed_partial_kernel      per-block FP64 sums of |u|^2 and s_ab s_ab
+//   ed_final_kernel        fixed-order sum of the block partials -> {E, eps}
+//   shell_partial_kernel   per-block shell sums of |u_hat|^2 / 2 (Eq. 27)
+//   shell_final_kernel     fixed-order sum over blocks
+// Every reduction runs in a fixed order for a given N, so results are
+// bitwise reproducible.
+#include "kin_common.cuh"
+#include "kin_internal.h"
+
+#include <cufft.h>
+
+namespace kin {
+
+size_t storage_bytes(int storage) {
+    switch (storage) {
+        case ST_F32: return 4;
+        case ST_F16: return 2;
+        case ST_BF16: return 2;
+        case ST_F64: return 8;
+    }
+    return 0;
+}
+
+// Canonical cell index of the stored element of population I for node x: the
+// LBE pull layout stores f_i(x) at x - xi_i.
+template <int I>
+__device__ __forceinline__ int stored_index(int x, int y, int z, int N, bool shifted) {
+    if (!shifted) return x + N * (y + N * z);
+    int xs = x - cx(I), ys = y - cy(I), zs = z - cz(I);
+    xs = xs < 0 ? xs + N : (xs >= N ? xs - N : xs);
+    ys = ys < 0 ? ys + N : (ys >= N ? ys - N : ys);
+    zs = zs < 0 ? zs + N : (zs >= N ? zs - N : zs);
+    return xs + N * (ys + N * zs);
+}
+
+__device__ __forceinline__ int stored_index_rt(int i, int x, int y, int z, int N, bool shifted) {
+    if (!shifted) return x + N * (y + N * z);
+    int xs = x - cx(i), ys = y - cy(i), zs = z - cz(i);
+    xs = xs < 0 ? xs + N : (xs >= N ? xs - N : xs);
+    ys = ys < 0 ? ys + N : (ys >= N ? ys - N : ys);
+    zs = zs < 0 ? zs + N : (zs >= N ? zs - N : zs);
+    return xs + N * (ys + N * zs);
+}
+
+template <typename S>
+__global__ void velocity_kernel(const S* __restrict__ st, bool shifted, int N, size_t plane,
+                                double* __restrict__ u) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    double jx = 0.0, jy = 0.0, jz = 0.0;
+    static_for<0, Q>([&](auto ic) {
+        constexpr int I = decltype(ic)::value;
+        const double v = (double)Traits<S>::load(st + I * plane + stored_index<I>(x, y, z, N, shifted));
+        if constexpr (cx(I) != 0) jx += cx(I) * v;
+        if constexpr (cy(I) != 0) jy += cy(I) * v;
+        if constexpr (cz(I) != 0) jz += cz(I) * v;
+    });
+    const size_t c = (size_t)x + (size_t)N * (y + (size_t)N * z);
+    u[c] = jx;
+    u[plane + c] = jy;
+    u[2 * plane + c] = jz;
+}
+
+constexpr int RED_THREADS = 256;
+
+int stats_blocks(int N) {
+    long long n = (long long)N * N * N;
+    long long b = (n + RED_THREADS * 8 - 1) / (RED_THREADS * 8);
+    if (b > 1216) b = 1216;  // 8 per SM on 152 SMs
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-then-warp reduction of |u|^2 and s_ab s_ab; each thread walks a fixed
+// grid-stride sequence of cells.
+__global__ void __launch_bounds__(RED_THREADS)
+    ed_partial_kernel(const double* __restrict__ u, int N, double* __restrict__ partial) {
+    const size_t n = (size_t)N * N * N;
+    double se = 0.0, ss = 0.0;
+    for (size_t c = (size_t)blockIdx.x * RED_THREADS + threadIdx.x; c < n;
+         c += (size_t)gridDim.x * RED_THREADS) {
+        const int x = (int)(c % N), y = (int)((c / N) % N), z = (int)(c / ((size_t)N * N));
+        const size_t nb[3][2] = {
+            {(size_t)wrap_inc(x, N) + (size_t)N * (y + (size_t)N * z),
+             (size_t)wrap_dec(x, N) + (size_t)N * (y + (size_t)N * z)},
+            {(size_t)x + (size_t)N * (wrap_inc(y, N) + (size_t)N * z),
+             (size_t)x + (size_t)N * (wrap_dec(y, N) + (size_t)N * z)},
+            {(size_t)x + (size_t)N * (y + (size_t)N * wrap_inc(z, N)),
+             (size_t)x + (size_t)N * (y + (size_t)N * wrap_dec(z, N))}};
+        double g[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) g[a][b] = 0.5 * (u[b * n + nb[a][0]] - u[b * n + nb[a][1]]);
+        double s2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const double sab = 0.5 * (g[a][b] + g[b][a]);
+                s2 += sab * sab;
+            }
+        ss += s2;
+        se += u[c] * u[c] + u[n + c] * u[n + c] + u[2 * n + c] * u[2 * n + c];
+    }
+    __shared__ double sh[2][RED_THREADS / 32];
+    se = warp_sum(se);
+    ss = warp_sum(ss);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[0][wid] = se;
+        sh[1][wid] = ss;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < RED_THREADS / 32; ++w) {
+            a += sh[0][w];
+            b += sh[1][w];
+        }
+        partial[2 * blockIdx.x] = a;
+        partial[2 * blockIdx.x + 1] = b;
+    }
+}
+
+__global__ void ed_final_kernel(const double* __restrict__ partial, int nblocks, size_t n, double nu,
+                                double* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nblocks; ++i) {
+        a += partial[2 * i];
+        b += partial[2 * i + 1];
+    }
+    out[0] = 0.5 * a / (double)n;
+    out[1] = 2.0 * nu * b / (double)n;
+}
+
+cudaError_t energy_dissipation(const double* u, int N, double nu, double* partials, double* out,
+                               cudaStream_t stream) {
+    const int nb = stats_blocks(N);
+    ed_partial_kernel<<<nb, RED_THREADS, 0, stream>>>(u, N, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ed_final_kernel<<<1, 32, 0, stream>>>(partials, nb, (size_t)N * N * N, nu, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Spectrum shells.  Modes of the half-complex layout [kz][ky][kx],
+// kx = 0..N/2; a mode with 0 < kx < N/2 also stands for its conjugate.
+// Lanes of a warp that fall in the same shell are summed in lane order by the
+// lowest lane, which adds the result to a warp-private shell array; the block
+// then adds its warps' arrays in warp order.
+constexpr int SPEC_THREADS = 256;
+
+int spectrum_blocks(int N) {
+    long long n = (long long)N * N * (N / 2 + 1);
+    long long b = (n + SPEC_THREADS * 16 - 1) / (SPEC_THREADS * 16);
+    if (b > 304) b = 304;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+__global__ void __launch_bounds__(SPEC_THREADS)
+    shell_partial_kernel(const double2* __restrict__ u0, const double2* __restrict__ u1,
+                         const double2* __restrict__ u2, int N, int nshell, double inv,
+                         int weight_n2, double* __restrict__ partial) {
+    extern __shared__ double bins[];  // [SPEC_THREADS/32][nshell]
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double* mybins = bins + wid * nshell;
+    for (int s = lane; s < nshell; s += 32) mybins[s] = 0.0;
+    __syncwarp();
+    const int nh = N / 2 + 1;
+    const size_t nmode = (size_t)N * N * nh;
+    // each warp handles consecutive chunks of 32 modes
+    const size_t nwarps = (size_t)gridDim.x * (SPEC_THREADS / 32);
+    const size_t gw = (size_t)blockIdx.x * (SPEC_THREADS / 32) + wid;
+    for (size_t base = gw * 32; base < nmode; base += nwarps * 32) {
+        const size_t m = base + lane;
+        int shell = -1;
+        double e = 0.0;
+        if (m < nmode) {
+            const int kx = (int)(m % nh);
+            const int ky = (int)((m / nh) % N);
+            const int kz = (int)(m / ((size_t)nh * N));
+            const int sy = ky > N / 2 ? ky - N : ky;
+            const int sz = kz > N / 2 ? kz - N : kz;
+            const long long n2 = (long long)kx * kx + (long long)sy * sy + (long long)sz * sz;
+            shell = (int)floor(sqrt((double)n2) + 0.5);
+            const double2 a = u0[m], b = u1[m], c = u2[m];
+            const double amp = (a.x * a.x + a.y * a.y) + (b.x * b.x + b.y * b.y) + (c.x * c.x + c.y * c.y);
+            const double w = (kx > 0 && 2 * kx < N) ? 2.0 : 1.0;
+            e = 0.5 * amp * inv * inv * w;
+            if (weight_n2) e *= (double)n2;
+        }
+        const unsigned same = __match_any_sync(0xffffffffu, shell);
+        const int leader = __ffs(same) - 1;
+        double acc = 0.0;
+        for (int l = 0; l < 32; ++l) {
+            const double v = __shfl_sync(0xffffffffu, e, l);
+            if ((same >> l) & 1u) acc += v;
+        }
+        if (lane == leader && shell >= 0 && shell < nshell) mybins[shell] += acc;
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < nshell; s += SPEC_THREADS) {
+        double a = 0.0;
+        for (int w = 0; w < SPEC_THREADS / 32; ++w) a += bins[w * nshell + s];
+        partial[(size_t)blockIdx.x * nshell + s] = a;
+    }
+}
+
+__global__ void shell_final_kernel(const double* __restrict__ partial, int nblocks, int nshell,
+                                   double* __restrict__ out) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nshell) return;
+    double a = 0.0;
+    for (int b = 0; b < nblocks; ++b) a += partial[(size_t)b * nshell + s];
+    out[s] = a;
+}
+
+cudaError_t spectrum_shells(const void* uh0, const void* uh1, const void* uh2, int N, int nshell,
+                            double inv, int weight_n2, double* partial, double* out,
+                            cudaStream_t stream) {
+    const int nb = spectrum_blocks(N);
+    const size_t smem = sizeof(double) * nshell * (SPEC_THREADS / 32);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(shell_partial_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    shell_partial_kernel<<<nb, SPEC_THREADS, smem, stream>>>(
+        (const double2*)uh0, (const double2*)uh1, (const double2*)uh2, N, nshell, inv, weight_n2,
+        partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    shell_final_kernel<<<(nshell + 127) / 128, 128, 0, stream>>>(partial, nb, nshell, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+template <typename S>
+__global__ void feq_kernel(const double* __restrict__ u, bool shifted, int N, size_t plane,
+                           S* __restrict__ st) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const size_t c = (size_t)x + (size_t)N * (y + (size_t)N * z);
+    const double ux = u[c], uy = u[plane + c], uz = u[2 * plane + c];
+    const double usq15 = 1.5 * (ux * ux + uy * uy + uz * uz);
+    static_for<0, Q>([&](auto ic) {
+        constexpr int I = decltype(ic)::value;
+        const double v = feq_i<I>(0.0, ux, uy, uz, usq15);
+        Traits<S>::store(st + I * plane + stored_index<I>(x, y, z, N, shifted),
+                         (typename Traits<S>::C)v);
+    });
+}
+
+template <typename S>
+__global__ void set_pop_kernel(int i, const double* __restrict__ pl, bool shifted, int N,
+                               size_t plane, S* __restrict__ st) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const size_t c = (size_t)x + (size_t)N * (y + (size_t)N * z);
+    Traits<S>::store(st + i * plane + stored_index_rt(i, x, y, z, N, shifted),
+                     (typename Traits<S>::C)pl[c]);
+}
+
+template <typename S>
+__global__ void get_pop_kernel(int i, const S* __restrict__ st, bool shifted, int N, size_t plane,
+                               double* __restrict__ pl) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const size_t c = (size_t)x + (size_t)N * (y + (size_t)N * z);
+    pl[c] = (double)Traits<S>::load(st + i * plane + stored_index_rt(i, x, y, z, N, shifted));
+}
+
+template <typename S>
+__global__ void sample_kernel(const S* __restrict__ st, bool shifted, int N, size_t plane,
+                              const int64_t* __restrict__ cells, int64_t n, double* __restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * Q) return;
+    const int64_t k = t / Q;
+    const int i = (int)(t % Q);
+    const int64_t c = cells[k];
+    const int x = (int)(c % N), y = (int)((c / N) % N), z = (int)(c / ((int64_t)N * N));
+    out[t] = (double)Traits<S>::load(st + i * plane + stored_index_rt(i, x, y, z, N, shifted));
+}
+
+__global__ void nonfinite_kernel(const double* __restrict__ v, size_t n, int* flag) {
+    bool bad = false;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(v[k]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+static dim3 row_grid(int N, int& bx) {
+    bx = N >= 128 ? 128 : ((N + 31) / 32) * 32;
+    return dim3((N + bx - 1) / bx, N, N);
+}
+
+#define KIN_DISPATCH(storage, CALL)                       \
+    switch (storage) {                                    \
+        case ST_F32: { using S = float; CALL; } break;    \
+        case ST_F16: { using S = __half; CALL; } break;   \
+        case ST_BF16: { using S = __nv_bfloat16; CALL; } break; \
+        case ST_F64: { using S = double; CALL; } break;   \
+        default: return cudaErrorInvalidValue;            \
+    }
+
+cudaError_t velocity_field(int storage, const void* state, bool shifted, int N, double* u,
+                           cudaStream_t stream) {
+    int bx;
+    dim3 g = row_grid(N, bx);
+    const size_t plane = (size_t)N * N * N;
+    KIN_DISPATCH(storage, (velocity_kernel<S><<<g, bx, 0, stream>>>((const S*)state, shifted, N, plane, u)));
+    return cudaGetLastError();
+}
+
+cudaError_t equilibrium_from_velocity(int storage, const double* u, bool shifted, int N,
+                                      void* state, cudaStream_t stream) {
+    int bx;
+    dim3 g = row_grid(N, bx);
+    const size_t plane = (size_t)N * N * N;
+    KIN_DISPATCH(storage, (feq_kernel<S><<<g, bx, 0, stream>>>(u, shifted, N, plane, (S*)state)));
+    return cudaGetLastError();
+}
+
+cudaError_t set_population(int storage, int i, const double* pl, bool shifted, int N, void* state,
+                           cudaStream_t stream) {
+    int bx;
+    dim3 g = row_grid(N, bx);
+    const size_t plane = (size_t)N * N * N;
+    KIN_DISPATCH(storage, (set_pop_kernel<S><<<g, bx, 0, stream>>>(i, pl, shifted, N, plane, (S*)state)));
+    return cudaGetLastError();
+}
+
+cudaError_t get_population(int storage, int i, const void* state, bool shifted, int N, double* pl,
+                           cudaStream_t stream) {
+    int bx;
+    dim3 g = row_grid(N, bx);
+    const size_t plane = (size_t)N * N * N;
+    KIN_DISPATCH(storage, (get_pop_kernel<S><<<g, bx, 0, stream>>>(i, (const S*)state, shifted, N, plane, pl)));
+    return cudaGetLastError();
+}
+
+cudaError_t sample_cells(int storage, const void* state, bool shifted, int N, const int64_t* cells,
+                         int64_t n, double* out, cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    const size_t plane = (size_t)N * N * N;
+    const int64_t tot = n * Q;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((tot + threads - 1) / threads);
+    KIN_DISPATCH(storage, (sample_kernel<S><<<blocks, threads, 0, stream>>>((const S*)state, shifted, N, plane, cells, n, out)));
+    return cudaGetLastError();
+}
+
+cudaError_t scan_nonfinite(const double* v, size_t n, int* flag, cudaStream_t stream) {
+    nonfinite_kernel<<<304, 256, 0, stream>>>(v, n, flag);
+    return cudaGetLastError();
+}
+
+}  // namespace kin
