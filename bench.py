@@ -35,6 +35,11 @@ METRIC = "LBE/DUGKS MLUPS at 256^3 FP32, % HBM roofline; ensemble p50/p99 latenc
 BYTES_PER_CELL = {"f32": 152, "f16": 76, "bf16": 76, "f64": 304}  # 19 loads + 19 stores
 K0, MA, RE_LAMBDA = 8.0, 0.15, 70.0
 STATS_EVERY, SPECTRUM_EVERY = 10, 200
+# The MRT-LBE run of this field goes non-finite after about 70 steps (a
+# stability result, reported under "stability"); every timed segment therefore
+# restarts both schemes from the seeded field, outside the timed region.
+SEGMENT = 50
+STABILITY_STEPS = 300
 
 
 def parse():
@@ -47,6 +52,7 @@ def parse():
     p.add_argument("--storage", choices=["f32", "f16", "bf16", "f64"], default="f32")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-stability", action="store_true")
     return p.parse_args()
 
 
@@ -234,25 +240,38 @@ def run_ours(args):
             lbe.stats(spectrum=spec)
             dug.stats(spectrum=spec)
 
+    def reinit():
+        lbe.init_field(seed, K0, RE_LAMBDA)
+        dug.init_field(seed, K0, RE_LAMBDA)
+
+    reinit()
     for k in range(args.warmup):
         bench_step(k)
     torch.cuda.synchronize()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    seg_ev = []
     launches0 = lbe.kernel_launches + dug.kernel_launches
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    start.record(stream)
-    for k in range(args.steps):
-        bench_step(k, evs[k])
-    stop.record(stream)
-    torch.cuda.synchronize()
+    done = 0
+    elapsed = 0.0
+    while done < args.steps:
+        n = min(SEGMENT, args.steps - done)
+        reinit()  # untimed: every segment starts from the seeded field
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for j in range(n):
+            bench_step(done + j, evs[done + j])
+        stop.record(stream)
+        torch.cuda.synchronize()
+        elapsed += start.elapsed_time(stop) / 1000.0
+        seg_ev.append(n)
+        done += n
     clocks.stop()
     launches = lbe.kernel_launches + dug.kernel_launches - launches0
-    elapsed = start.elapsed_time(stop) / 1000.0
     t_lbe = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps / 1000.0
     t_dug = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps / 1000.0
     tmax = elapsed
@@ -274,7 +293,7 @@ def run_ours(args):
         pinned = torch.empty(u0.shape, dtype=torch.float64, pin_memory=True)
         pinned.numpy()[...] = u0
         hu = pinned.numpy()
-        k_e2e = max(10, min(args.steps, 200))
+        k_e2e = max(10, min(args.steps, SEGMENT))
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
@@ -297,6 +316,24 @@ def run_ours(args):
                "steps": k_e2e,
                "what": "kin_set_velocity from pinned host memory for both schemes, then per step "
                        "kin_step(1) and kin_stats(E, eps) of each; host wall clock"}
+
+    # stability probe (untimed): first check at which E is non-finite, every 5
+    # steps up to STABILITY_STEPS, from the seeded field
+    stability = {}
+    for name, sim in (() if args.no_stability else (("lbe", lbe), ("dugks", dug))):
+        sim.init_field(seed, K0, RE_LAMBDA)
+        bad = None
+        for n in range(0, STABILITY_STEPS + 1, 5):
+            try:
+                sim.stats()
+            except kin.KinError as exc:
+                if exc.code != kin.KIN_ENONFINITE:
+                    raise
+                bad = n
+                break
+            sim.step(5)
+        stability[name] = {"nonfinite_at_step": bad, "checked_through_step": STABILITY_STEPS,
+                           "nu": sim.nu}
 
     peak, peak_kind = _peaks()
     bpc = BYTES_PER_CELL[args.storage]
@@ -329,6 +366,8 @@ def run_ours(args):
         "clocks": clocks.summary(),
         "gpu_launches": launches * world,
         "e2e": e2e,
+        "stability": stability,
+        "timing": "%d segments of up to %d steps, each from the seeded field" % (len(seg_ev), SEGMENT),
     }
     for sim in (lbe, dug):
         sim.close()
