@@ -121,6 +121,16 @@ int kin_stats(kin_sim* sim, double* E, double* eps, double* Ek);
 /* Number of spectrum shells for edge N: 1 + floor(sqrt(3) (N/2) + 1/2). */
 int kin_num_shells(int N);
 
+/* Launch-shape tuning (all values <= 0 keep the current setting):
+ *   block_x  LBE: threads per block along x (multiple of 32, <= 1024)
+ *   tile_y   DUGKS fused kernel: rows per tile, 4 or 8
+ *   zchunk   DUGKS fused kernel: planes each thread block marches through
+ *   variant  DUGKS: 0 = fused single launch (default), 1 = two launches
+ *            (pre-step into scratch, then flux + update)
+ * Results do not depend on the launch shape or variant beyond rounding
+ * order (the fused and two-launch forms sum the same terms differently). */
+int kin_set_tuning(kin_sim* sim, int block_x, int tile_y, int zchunk, int variant);
+
 /* Number of kernel launches one kin_step(sim, 1) enqueues. */
 int kin_step_launches(const kin_sim* sim);
 

@@ -68,6 +68,7 @@ def _declare(lib):
         "kin_num_shells": (c_int, [c_int]),
         "kin_sync": (c_int, [P]),
         "kin_step_launches": (c_int, [P]),
+        "kin_set_tuning": (c_int, [P, c_int, c_int, c_int, c_int]),
         "kin_kernel_launches": (c_i64, [P]),
         "kin_get_nu": (c_double, [P]),
         "kin_get_dt": (c_double, [P]),
@@ -224,6 +225,10 @@ class Sim:
         if spectrum:
             return float(E[0]), float(eps[0]), Ek
         return float(E[0]), float(eps[0])
+
+    def set_tuning(self, block_x: int = 0, tile_y: int = 0, zchunk: int = 0, variant: int = -1):
+        _check(lib().kin_set_tuning(self._h, int(block_x), int(tile_y), int(zchunk), int(variant)),
+               "kin_set_tuning")
 
     @property
     def step_launches(self) -> int:

@@ -33,6 +33,7 @@ struct kin_sim {
     cufftHandle d2z = 0, z2d = 0;
     bool have_d2z = false, have_z2d = false;
     int block_lbe = 0, block_dugks = 0;
+    int tile_y = 8, zchunk = 32, variant = 0;
     int64_t launches = 0;  // own kernel launches
 };
 
@@ -110,8 +111,10 @@ int launch_step(kin_sim* s) {
     cudaError_t e;
     if (s->scheme == KIN_LBE_MRT)
         e = lbe_step(s->storage, src, dst, s->N, s->nu, s->block_lbe, s->stream);
-    else
+    else if (s->variant == 1)
         e = dugks_step(s->storage, src, dst, s->fbp, s->N, s->nu, s->dt, s->block_dugks, s->stream);
+    else
+        e = dugks_step_fused(s->storage, src, dst, s->N, s->nu, s->dt, s->tile_y, s->zchunk, s->stream);
     if (e != cudaSuccess) return fail(KIN_ECUDA, "step launch: %s", cudaGetErrorString(e));
     s->launches += kin_step_launches(s);
     s->cur ^= 1;
@@ -137,9 +140,8 @@ int kin_lattice(int* xi, double* w) {
 size_t kin_footprint_bytes(int N, int scheme, int storage) {
     if (N < 2 || storage < 0 || storage > 3) return 0;
     const size_t n = (size_t)N * N * N;
-    size_t b = 2 * Q * n * storage_bytes(storage);
-    if (scheme == KIN_DUGKS) b += Q * n * dugks_scratch_bytes(storage);
-    return b;
+    (void)scheme;
+    return 2 * Q * n * storage_bytes(storage);
 }
 
 int kin_num_shells(int N) {
@@ -191,14 +193,6 @@ int kin_create(int N, int scheme, double nu, double Ma, double dt, int storage, 
         }
         e = cudaMemsetAsync(s->buf[k], 0, sb, s->stream);
         if (e != cudaSuccess) return bail(fail(KIN_ECUDA, "memset: %s", cudaGetErrorString(e)));
-    }
-    if (scheme == KIN_DUGKS) {
-        const size_t fb = Q * ncell(s) * dugks_scratch_bytes(storage);
-        cudaError_t e = cudaMalloc(&s->fbp, fb);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return bail(fail(KIN_ENOMEM, "DUGKS scratch of %zu bytes: %s", fb, cudaGetErrorString(e)));
-        }
     }
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return bail(fail(KIN_ECUDA, "sync: %s", cudaGetErrorString(e)));
@@ -413,7 +407,25 @@ int kin_stats(kin_sim* s, double* E, double* eps, double* Ek) {
 
 int kin_step_launches(const kin_sim* s) {
     if (!s) return 0;
-    return s->scheme == KIN_LBE_MRT ? 1 : 2;
+    if (s->scheme == KIN_LBE_MRT) return 1;
+    return s->variant == 1 ? 2 : 1;
+}
+
+int kin_set_tuning(kin_sim* s, int block_x, int tile_y, int zchunk, int variant) {
+    if (int r = valid(s)) return r;
+    if (block_x > 0 && (block_x % 32 || block_x > 1024)) return fail(KIN_EINVAL, "block_x %d", block_x);
+    if (tile_y > 0 && tile_y != 4 && tile_y != 8) return fail(KIN_EINVAL, "tile_y must be 4 or 8");
+    if (variant > 1) return fail(KIN_EINVAL, "variant %d", variant);
+    if (variant == 1 && s->scheme == KIN_DUGKS && !s->fbp) {
+        const size_t fb = Q * ncell(s) * dugks_scratch_bytes(s->storage);
+        DeviceGuard g(s->device);
+        CK(cudaMalloc(&s->fbp, fb));
+    }
+    if (block_x > 0) s->block_lbe = s->block_dugks = block_x;
+    if (tile_y > 0) s->tile_y = tile_y;
+    if (zchunk > 0) s->zchunk = zchunk;
+    if (variant >= 0) s->variant = variant;
+    return KIN_OK;
 }
 
 int64_t kin_kernel_launches(const kin_sim* s) { return s ? s->launches : 0; }

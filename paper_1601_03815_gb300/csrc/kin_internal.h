@@ -24,6 +24,11 @@ cudaError_t lbe_step(int storage, const void* src, void* dst, int N, double nu, 
 cudaError_t dugks_step(int storage, const void* src, void* dst, void* fbp, int N, double nu,
                        double dt, int block_x, cudaStream_t stream);
 
+// Fused single-launch DUGKS step; tile_y in {4, 8} (FP64 always uses 4),
+// zchunk planes per CTA.
+cudaError_t dugks_step_fused(int storage, const void* src, void* dst, int N, double nu, double dt,
+                             int tile_y, int zchunk, cudaStream_t stream);
+
 // Compute-type size of the DUGKS scratch element (4 or 8 bytes).
 size_t dugks_scratch_bytes(int storage);
 

@@ -40,13 +40,18 @@ def _scheme(kin, name):
     return kin.LBE_MRT if name == "lbe" else kin.DUGKS
 
 
-@pytest.mark.parametrize("scheme", ["lbe", "dugks"])
+@pytest.mark.parametrize("scheme", ["lbe", "dugks", "dugks-split", "dugks-ty4"])
 @pytest.mark.parametrize("storage", [3, 0, 1, 2])
 @pytest.mark.parametrize("N", [2, 5, 12, 33])
 def test_one_step_parity(kin, orc, scheme, storage, N):
     nu, dt = 0.013, (1.0 if scheme == "lbe" else 0.5)
     f0 = _state(orc, N, 100 + N)
     sim = kin.Sim(N, _scheme(kin, scheme), nu, 0.1, dt, storage)
+    if scheme == "dugks-split":
+        sim.set_tuning(variant=1)
+    elif scheme == "dugks-ty4":
+        sim.set_tuning(tile_y=4, zchunk=3)
+    scheme = scheme.split("-")[0]
     sim.set_f(f0)
     f_in = sim.get_f()  # the stored (rounded) state is what the GPU steps from
     if storage == 3:
@@ -58,13 +63,17 @@ def test_one_step_parity(kin, orc, scheme, storage, N):
     sim.close()
 
 
-@pytest.mark.parametrize("scheme", ["lbe", "dugks"])
+@pytest.mark.parametrize("scheme", ["lbe", "dugks", "dugks-ty4"])
 def test_one_step_parity_ragged_large(kin, orc, scheme):
-    """Sizes spanning several thread blocks with a ragged tail in x."""
-    N = 130 if scheme == "lbe" else 66
+    """Sizes spanning several thread blocks and z chunks with ragged tails
+    (x tiles of 30 and 128, y tiles of 4 and 8, z chunks of 32 and 7)."""
+    N = 130 if scheme == "lbe" else 67
     nu, dt = 0.02, (1.0 if scheme == "lbe" else 0.35355)
     f0 = _state(orc, N, 5)
     sim = kin.Sim(N, _scheme(kin, scheme), nu, 0.1, dt, kin.F32)
+    if scheme == "dugks-ty4":
+        sim.set_tuning(tile_y=4, zchunk=7)
+    scheme = scheme.split("-")[0]
     sim.set_f(f0)
     sim.step(1)
     assert _err(sim.get_f(), orc.step(scheme, f0, nu, dt)) < 1e-5
