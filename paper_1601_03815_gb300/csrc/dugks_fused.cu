@@ -55,6 +55,35 @@ struct FusedSmem {
     C fy[NF][TY + 1][32];
 };
 
+// Raw f-tilde staging for 4-byte storage, filled by cp.async: planes z - 1 and
+// z (awaiting their update), z + 1 (next pre-step) and z + 2 (in flight while
+// plane z is computed).  Other storage types read global memory directly.
+template <typename S, int TY>
+struct RawStage {
+    S raw[4][Q][TY + 2][32];
+};
+
+template <typename S>
+constexpr bool kAsyncStage = sizeof(S) == 4;
+
+template <typename S>
+__device__ __forceinline__ void cp_async_elem(S* smem_dst, const S* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if constexpr (sizeof(S) == 4) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+    } else {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+    }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <typename S, int TY>
+constexpr size_t fused_smem_bytes() {
+    using C = typename Traits<S>::C;
+    return sizeof(FusedSmem<C, TY>) + (kAsyncStage<S> ? sizeof(RawStage<S, TY>) : 0);
+}
+
 template <typename C>
 struct CellView {
     // tangential differences G[t][k] for population flux_pop(t, k)
@@ -177,12 +206,13 @@ __device__ __forceinline__ int wrapc(int v, int n) {
 }
 
 template <typename S, int TY>
-__global__ void __launch_bounds__(32 * (TY + 2))
+__global__ void __launch_bounds__(32 * (TY + 2), 1)
     dugks_fused_kernel(const S* __restrict__ src, S* __restrict__ dst, int N, int zchunk,
                        DugksCoef<typename Traits<S>::C> kc) {
     using C = typename Traits<S>::C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FusedSmem<C, TY>& sm = *reinterpret_cast<FusedSmem<C, TY>*>(smem_raw);
+    RawStage<S, TY>* stage = reinterpret_cast<RawStage<S, TY>*>(smem_raw + sizeof(FusedSmem<C, TY>));
 
     const int lane = threadIdx.x, row = threadIdx.y;
     const int x0 = blockIdx.x * 30, y0 = blockIdx.y * TY, z0 = blockIdx.z * zchunk;
@@ -197,15 +227,36 @@ __global__ void __launch_bounds__(32 * (TY + 2))
     const size_t colidx = (size_t)gx + (size_t)N * gy;
     const size_t nn = (size_t)N * N;
     const C h = kc.h, hq = C(0.25) * kc.h;
+    // x neighbours, clamped so the two halo lanes can run the interior code
+    // path (their x differences are never used)
+    const int lp = min(lane + 1, 31), lm = max(lane - 1, 0);
 
+    // ring slots hold fbp of planes z-1, z, z+1; raw slots hold f-tilde of
+    // planes z-1 (update), z (next update), z+1 (next pre-step), z+2 (in flight)
     auto slot_of = [&](int z) { return (z - z0 + 3) % 3; };
+    auto rslot_of = [&](int z) { return (z - z0 + 4) & 3; };
 
+    auto issue_plane = [&](int z) {
+        if constexpr (kAsyncStage<S>) {
+            const S* p = src + (size_t)wrapc(z, N) * nn + colidx;
+            const int s = rslot_of(z);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) cp_async_elem(&stage->raw[s][i][row][lane], p + i * plane);
+            cp_async_commit();
+        }
+    };
+    auto raw_value = [&](int z, int i) -> C {
+        if constexpr (kAsyncStage<S>) {
+            return (C)stage->raw[rslot_of(z)][i][row][lane];
+        } else {
+            return Traits<S>::load(src + (size_t)wrapc(z, N) * nn + colidx + i * plane);
+        }
+    };
     // Eq. 19 for this thread's column at plane z into the ring.
-    auto load_plane = [&](int z) {
-        const S* p = src + (size_t)wrapc(z, N) * nn + colidx;
+    auto prestep = [&](int z) {
         C f[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) f[i] = Traits<S>::load(p + i * plane);
+        for (int i = 0; i < Q; ++i) f[i] = raw_value(z, i);
         C drho, jx, jy, jz;
         moments(f, drho, jx, jy, jz);
         const C usq15 = C(1.5) * (jx * jx + jy * jy + jz * jz);
@@ -215,8 +266,7 @@ __global__ void __launch_bounds__(32 * (TY + 2))
             sm.ring[s][I][row][lane] = kc.a * f[I] + kc.b * feq_i<I>(drho, jx, jy, jz, usq15);
         });
     };
-
-    // Cell view at the ring slot `s`, tangential differences for the axes in MASK.
+    // Cell view at ring slot s with the tangential differences in MASK.
     auto gather = [&](int s, int sm1, int sp1, auto maskc, CellView<C>& v) {
         constexpr int MASK = decltype(maskc)::value;
 #pragma unroll
@@ -228,7 +278,7 @@ __global__ void __launch_bounds__(32 * (TY + 2))
                     constexpr int K = decltype(kc2)::value;
                     constexpr int I = flux_pop(T, K);
                     C g;
-                    if constexpr (T == 0) g = sm.ring[s][I][row][lane + 1] - sm.ring[s][I][row][lane - 1];
+                    if constexpr (T == 0) g = sm.ring[s][I][row][lp] - sm.ring[s][I][row][lm];
                     else if constexpr (T == 1) g = sm.ring[s][I][row + 1][lane] - sm.ring[s][I][row - 1][lane];
                     else g = sm.ring[sp1][I][row][lane] - sm.ring[sm1][I][row][lane];
                     v.G[T][K] = g;
@@ -239,36 +289,43 @@ __global__ void __launch_bounds__(32 * (TY + 2))
         cell_diffs<MASK>(v);
     };
 
-    C zdn[NF];  // flux through the face below the plane being updated
-    load_plane(z0 - 1);
-    load_plane(z0);
+    issue_plane(z0 - 1);
+    issue_plane(z0);
+    cp_async_wait_all();
+    prestep(z0 - 1);
+    prestep(z0);
+    issue_plane(z0 + 1);
     __syncthreads();
+    C Pz[NREC];   // P^z record of the plane below the current one
+    C Dprev[Q];   // face-flux sum of plane z-1, still missing its +z face
     if (interior) {
         CellView<C> v;
-        C Pz[NREC], Mz[NREC];
         gather(slot_of(z0 - 1), 0, 0, std::integral_constant<int, 3>{}, v);
         side_record<2, +1>(v, h, hq, Pz);
-        gather(slot_of(z0), 0, 0, std::integral_constant<int, 3>{}, v);
-        side_record<2, -1>(v, h, hq, Mz);
-        face_from_records<2>(Pz, Mz, kc, zdn);
     }
-
-    for (int z = z0; z < zend; ++z) {
-        load_plane(z + 1);
-        __syncthreads();
-        const int s0 = slot_of(z), sm1 = slot_of(z - 1), sp1 = slot_of(z + 1);
-        C D[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) D[i] = C(0);
+    for (int i = 0; i < Q; ++i) Dprev[i] = C(0);
+
+    for (int z = z0; z <= zend; ++z) {
+        const bool last = z == zend;
+        if (!last) {
+            if constexpr (kAsyncStage<S>) cp_async_wait_all();
+            prestep(z + 1);
+            if (z + 2 <= zend) issue_plane(z + 2);
+        }
+        __syncthreads();  // ring slot of z + 1 complete; fy of plane z - 1 complete
+        C Dcur[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Dcur[i] = C(0);
         C Py[NREC];
-        {
-            // plane z: x records (rows 1..TY, all lanes), y records (lanes 1..30, all rows)
+        if (!last) {
+            const int s0 = slot_of(z), sm1 = slot_of(z - 1), sp1 = slot_of(z + 1);
             CellView<C> v;
-            if (yin && xin) {
+            // warp-uniform: rows 1..TY take every difference, the halo rows
+            // only those their y records need
+            if (yin) {
                 gather(s0, sm1, sp1, std::integral_constant<int, 7>{}, v);
-            } else if (yin) {
-                gather(s0, sm1, sp1, std::integral_constant<int, 6>{}, v);  // G^y, G^z
-            } else if (xin) {
+            } else {
                 gather(s0, sm1, sp1, std::integral_constant<int, 5>{}, v);  // G^x, G^z
             }
             C Px[NREC], Mx[NREC];
@@ -295,25 +352,51 @@ __global__ void __launch_bounds__(32 * (TY + 2))
             if (interior) {
                 static_for<0, NF>([&](auto kc2) {
                     constexpr int K = decltype(kc2)::value;
-                    D[flux_pop(0, K)] += Fx[K] - Fl[K];
+                    Dcur[flux_pop(0, K)] += Fx[K] - Fl[K];
                 });
-                // z faces: (z, z+1) from P^z(z) and M^z(z+1)
-                C Pz[NREC], Mz[NREC], Fz[NF];
-                side_record<2, +1>(v, h, hq, Pz);
-                CellView<C> w;
-                gather(sp1, 0, 0, std::integral_constant<int, 3>{}, w);
-                side_record<2, -1>(w, h, hq, Mz);
+                // z face (z-1, z): P^z(z-1) carried, M^z(z) from this view
+                C Mz[NREC], Fz[NF];
+                side_record<2, -1>(v, h, hq, Mz);
                 face_from_records<2>(Pz, Mz, kc, Fz);
                 static_for<0, NF>([&](auto kc2) {
                     constexpr int K = decltype(kc2)::value;
-                    D[flux_pop(2, K)] += Fz[K] - zdn[K];
-                    zdn[K] = Fz[K];
+                    Dprev[flux_pop(2, K)] += Fz[K];
+                    Dcur[flux_pop(2, K)] -= Fz[K];
                 });
+                side_record<2, +1>(v, h, hq, Pz);
+            }
+        } else if (interior) {
+            CellView<C> v;
+            C Mz[NREC], Fz[NF];
+            gather(slot_of(z), 0, 0, std::integral_constant<int, 3>{}, v);
+            side_record<2, -1>(v, h, hq, Mz);
+            face_from_records<2>(Pz, Mz, kc, Fz);
+            static_for<0, NF>([&](auto kc2) {
+                constexpr int K = decltype(kc2)::value;
+                Dprev[flux_pop(2, K)] += Fz[K];
+            });
+        }
+        // update plane z - 1 (Eqs. 20, 9): its y faces were computed one iteration ago
+        if (z > z0 && interior) {
+            static_for<0, NF>([&](auto kc2) {
+                constexpr int K = decltype(kc2)::value;
+                Dprev[flux_pop(1, K)] += sm.fy[K][row][lane] - sm.fy[K][row - 1][lane];
+            });
+            if (valid) {
+                const size_t c = (size_t)(z - 1) * nn + colidx;
+                const int sp = slot_of(z - 1);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const C ft = raw_value(z - 1, i);
+                    const C fb = sm.ring[sp][i][row][lane];
+                    Traits<S>::store(dst + i * plane + c,
+                                     C(4.0 / 3.0) * fb - C(1.0 / 3.0) * ft - kc.dt * Dprev[i]);
+                }
             }
         }
-        __syncthreads();
-        // y faces: face r between rows r and r + 1, for r = 0..TY
-        if (xin && row <= TY) {
+        __syncthreads();  // my of plane z complete; fy of plane z - 1 consumed
+        if (!last && xin && row <= TY) {
+            // y faces of plane z: face r between rows r and r + 1, r = 0..TY
             C Mu[NREC], Fy[NF];
 #pragma unroll
             for (int r = 0; r < NREC; ++r) Mu[r] = sm.my[r][row + 1][lane];
@@ -321,32 +404,15 @@ __global__ void __launch_bounds__(32 * (TY + 2))
 #pragma unroll
             for (int r = 0; r < NF; ++r) sm.fy[r][row][lane] = Fy[r];
         }
-        __syncthreads();
-        if (interior) {
-            static_for<0, NF>([&](auto kc2) {
-                constexpr int K = decltype(kc2)::value;
-                D[flux_pop(1, K)] += sm.fy[K][row][lane] - sm.fy[K][row - 1][lane];
-            });
-            if (valid) {
-                // Eq. 20 and Eq. 9: f-tilde^{n+1} = 4/3 fbp - 1/3 f-tilde - dt sum of face fluxes
-                const size_t c = (size_t)z * nn + colidx;
 #pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    const C ft = Traits<S>::load(src + i * plane + c);
-                    const C fb = sm.ring[s0][i][row][lane];
-                    Traits<S>::store(dst + i * plane + c,
-                                     C(4.0 / 3.0) * fb - C(1.0 / 3.0) * ft - kc.dt * D[i]);
-                }
-            }
-        }
+        for (int i = 0; i < Q; ++i) Dprev[i] = Dcur[i];
     }
 }
 
 template <typename S, int TY>
 static cudaError_t launch_fused_t(const void* src, void* dst, int N, int zchunk,
                                   const DugksCoef<typename Traits<S>::C>& k, cudaStream_t stream) {
-    using C = typename Traits<S>::C;
-    const size_t smem = sizeof(FusedSmem<C, TY>);
+    const size_t smem = fused_smem_bytes<S, TY>();
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(dugks_fused_kernel<S, TY>,
