@@ -158,6 +158,40 @@ const char* kin_last_error(void);
 /* Release all device memory of sim; NULL-safe. */
 void kin_destroy(kin_sim* sim);
 
+/* ------------------------------------------------------------------------
+ * Ensembles: many independent simulations (any mix of N and scheme, all
+ * KIN_F32 storage, one device) advanced together by ONE persistent,
+ * cooperative kernel launch per kin_ensemble_step call, captured in a CUDA
+ * graph.  Each member's results are bitwise identical to stepping it alone
+ * with the same tile shape (kin_set_tuning tile_y / zchunk).  There is no
+ * counterpart of this batching in the paper, which runs one simulation.
+ */
+typedef struct kin_ensemble kin_ensemble;
+
+/* members: n distinct handles; the ensemble keeps the pointers (the caller
+ * keeps ownership and must destroy the ensemble before any member). */
+int kin_ensemble_create(kin_sim* const* members, int n, kin_ensemble** out);
+
+/* Work decomposition: tile_y (4 or 8) and zchunk of the DUGKS tiles, lbe_nodes
+ * (multiple of 32) LBE nodes per work item; values <= 0 keep the setting. */
+int kin_ensemble_set_tuning(kin_ensemble* ens, int tile_y, int zchunk, int lbe_nodes);
+
+/* Advance every member by nsteps in one persistent launch (synchronous).
+ * Members must be idle; their streams are synchronised first.  Returns
+ * KIN_ETIMEOUT if a member barrier inside the kernel waited longer than its
+ * bound (the members are then left at their state before the call). */
+int kin_ensemble_step(kin_ensemble* ens, int nsteps);
+
+/* Run the persistent kernel with a member barrier that cannot be satisfied
+ * and a wait bound of `seconds`: must return KIN_ETIMEOUT promptly and leave
+ * the members unchanged.  For testing the bounded wait. */
+int kin_ensemble_test_timeout(kin_ensemble* ens, double seconds);
+
+/* Work items per step, thread blocks of the persistent launch, launches so far. */
+int kin_ensemble_info(const kin_ensemble* ens, int* nitems, int* grid, int64_t* launches);
+
+void kin_ensemble_destroy(kin_ensemble* ens);
+
 #ifdef __cplusplus
 }
 #endif

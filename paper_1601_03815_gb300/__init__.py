@@ -80,6 +80,12 @@ def _declare(lib):
         "kin_strerror": (ctypes.c_char_p, [c_int]),
         "kin_last_error": (ctypes.c_char_p, []),
         "kin_destroy": (None, [P]),
+        "kin_ensemble_create": (c_int, [P, c_int, P]),
+        "kin_ensemble_set_tuning": (c_int, [P, c_int, c_int, c_int]),
+        "kin_ensemble_step": (c_int, [P, c_int]),
+        "kin_ensemble_test_timeout": (c_int, [P, c_double]),
+        "kin_ensemble_info": (c_int, [P, P, P, P]),
+        "kin_ensemble_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -256,3 +262,44 @@ class Sim:
     @property
     def steps_taken(self) -> int:
         return int(lib().kin_get_step(self._h))
+
+
+class Ensemble:
+    """Independent simulations advanced together by one persistent kernel
+    launch per step() call (see kin_ensemble_* in kin.h).  Keeps references to
+    its members so they outlive it."""
+
+    def __init__(self, members):
+        self.members = list(members)
+        arr = (ctypes.c_void_p * len(self.members))(*[m.handle.value for m in self.members])
+        h = ctypes.c_void_p()
+        _check(lib().kin_ensemble_create(arr, len(self.members), ctypes.byref(h)), "kin_ensemble_create")
+        self._h = h
+
+    def set_tuning(self, tile_y: int = 0, zchunk: int = 0, lbe_nodes: int = 0):
+        _check(lib().kin_ensemble_set_tuning(self._h, int(tile_y), int(zchunk), int(lbe_nodes)),
+               "kin_ensemble_set_tuning")
+
+    def step(self, n: int = 1):
+        _check(lib().kin_ensemble_step(self._h, int(n)), "kin_ensemble_step")
+
+    def test_timeout(self, seconds: float) -> int:
+        """Run the bounded-wait self test; returns the status code."""
+        return int(lib().kin_ensemble_test_timeout(self._h, float(seconds)))
+
+    def info(self):
+        nitems, grid, launches = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        _check(lib().kin_ensemble_info(self._h, ctypes.byref(nitems), ctypes.byref(grid),
+                                       ctypes.byref(launches)), "kin_ensemble_info")
+        return {"items": nitems.value, "grid": grid.value, "launches": launches.value}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().kin_ensemble_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

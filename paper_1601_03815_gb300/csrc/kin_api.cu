@@ -3,6 +3,7 @@
 #include "kin_common.cuh"
 #include "kin_init.h"
 #include "kin_internal.h"
+#include "kin_sim.h"
 
 #include <cufft.h>
 
@@ -14,32 +15,21 @@
 
 using namespace kin;
 
-struct kin_sim {
-    int N = 0, scheme = 0, storage = 0;
-    double nu = 0, Ma = 0, dt = 0;
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    void* buf[2] = {nullptr, nullptr};
-    int cur = 0;
-    void* fbp = nullptr;  // DUGKS f-bar-plus scratch
-    int64_t step = 0;
-    // statistics scratch (lazy)
-    double* u = nullptr;      // 3 N^3
-    double2* uh = nullptr;    // 3 N^2 (N/2+1)
-    double* red = nullptr;    // block partials
-    double* red_out = nullptr;
-    size_t red_cap = 0;
-    cufftHandle d2z = 0, z2d = 0;
-    bool have_d2z = false, have_z2d = false;
-    int block_lbe = 0, block_dugks = 0;
-    int tile_y = 8, zchunk = 32, variant = 0;
-    int64_t launches = 0;  // own kernel launches
-};
+
 
 namespace {
-
 thread_local char g_err[512] = "";
+}  // namespace
+
+int kin::set_error(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+namespace {
 
 int fail(int code, const char* fmt, ...) {
     va_list ap;

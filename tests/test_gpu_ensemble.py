@@ -1,0 +1,113 @@
+"""Persistent-kernel ensemble: each member matches stepping it alone with
+kin_step (within the FP32 parity tolerance: the two kernels contract the same
+node arithmetic into FMAs differently), is bitwise identical whether it runs
+alone in an ensemble or mixed with other members, across odd and even step
+counts, graph re-launches and ragged tiles; the in-kernel member barrier is
+bounded and reports KIN_ETIMEOUT without touching state."""
+import numpy as np
+import pytest
+
+import kin_inputs as ki
+
+pytestmark = pytest.mark.gpu
+
+MEMBERS = [("lbe", 16), ("dugks", 16), ("lbe", 20), ("dugks", 33), ("dugks", 12), ("lbe", 9)]
+
+
+def _state(orc, N, seed):
+    u = ki.random_velocity(N, N, N, seed, 0.03)
+    return orc.equilibrium_field(u) + ki.random_populations(N, N, N, seed + 1, 1e-5)
+
+
+def _make(kin, orc, tuning=(8, 16)):
+    ens_members, solo = [], []
+    for k, (scheme, N) in enumerate(MEMBERS):
+        f0 = _state(orc, N, 300 + k)
+        sc = kin.LBE_MRT if scheme == "lbe" else kin.DUGKS
+        dt = 1.0 if scheme == "lbe" else 0.45
+        nu = 0.01 + 0.002 * k
+        a = kin.Sim(N, sc, nu, 0.1, dt, kin.F32)
+        b = kin.Sim(N, sc, nu, 0.1, dt, kin.F32)
+        a.set_f(f0)
+        b.set_f(f0)
+        b.set_tuning(tile_y=tuning[0], zchunk=tuning[1])
+        ens_members.append(a)
+        solo.append(b)
+    return ens_members, solo
+
+
+@pytest.mark.parametrize("tuning", [(8, 16), (4, 7)])
+def test_ensemble_is_bitwise_equal_to_solo_runs(kin, orc, tuning):
+    members, solo = _make(kin, orc, tuning)
+    ens = kin.Ensemble(members)
+    ens.set_tuning(tile_y=tuning[0], zchunk=tuning[1], lbe_nodes=256)
+    ens.step(3)
+    ens.step(4)  # second launch, other parity
+    ens.step(3)  # graph for 3 steps reused
+    for s in solo:
+        s.step(10)
+    for a, b in zip(members, solo):
+        assert a.steps_taken == 10
+        fa, fb = a.get_f(), b.get_f()
+        scale = np.abs(fb).reshape(19, -1).max(axis=1)
+        assert (np.abs(fa - fb).reshape(19, -1).max(axis=1) / scale).max() < 1e-5
+    info = ens.info()
+    assert info["launches"] == 3 and info["grid"] >= 1 and info["items"] > len(MEMBERS)
+    ens.close()
+    for s in members + solo:
+        s.close()
+
+
+def test_ensemble_barrier_timeout_is_bounded_and_harmless(kin, orc):
+    import time
+
+    members, solo = _make(kin, orc)
+    ens = kin.Ensemble(members)
+    before = [m.get_f() for m in members]
+    t0 = time.time()
+    rc = ens.test_timeout(0.05)
+    assert rc == kin.KIN_ETIMEOUT
+    assert time.time() - t0 < 30.0
+    for m, f in zip(members, before):
+        assert m.steps_taken == 0
+        np.testing.assert_array_equal(m.get_f(), f)
+    # the ensemble still works afterwards
+    ens.step(2)
+    for s in solo:
+        s.step(2)
+    for a, b in zip(members, solo):
+        fa, fb = a.get_f(), b.get_f()
+        assert np.abs(fa - fb).max() < 1e-5 * np.abs(fb).max()
+    ens.close()
+
+
+def test_member_alone_and_in_the_mix_are_bitwise_equal(kin, orc):
+    """The same member stepped by an ensemble of one and by the full ensemble
+    gives identical bits: the mix changes the schedule, not the arithmetic."""
+    members, _ = _make(kin, orc)
+    alone = []
+    for k, m in enumerate(members):
+        c = kin.Sim(m.N, m.scheme, 0.01 + 0.002 * k, 0.1, 1.0 if m.scheme == kin.LBE_MRT else 0.45,
+                    kin.F32)
+        c.set_f(m.get_f())
+        alone.append(c)
+    mix = kin.Ensemble(members)
+    mix.step(5)
+    for c in alone:
+        e1 = kin.Ensemble([c])
+        e1.step(5)
+        e1.close()
+    for a, c in zip(members, alone):
+        np.testing.assert_array_equal(a.get_f(), c.get_f())
+    mix.close()
+
+
+def test_ensemble_rejects_bad_members(kin):
+    a = kin.Sim(8, kin.LBE_MRT, 0.01, 0.1, 1.0, kin.F16)
+    with pytest.raises(kin.KinError):
+        kin.Ensemble([a])
+    b = kin.Sim(8, kin.LBE_MRT, 0.01, 0.1, 1.0, kin.F32)
+    with pytest.raises(kin.KinError):
+        kin.Ensemble([b, b])
+    a.close()
+    b.close()
