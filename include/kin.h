@@ -118,6 +118,23 @@ int kin_step(kin_sim* sim, int n);
  * Returns KIN_ENONFINITE if E is not finite. */
 int kin_stats(kin_sim* sim, double* E, double* eps, double* Ek);
 
+/* E and eps (as in kin_stats) of a velocity field u[3][N^3] (FP64, x fastest)
+ * that is already in device memory, written to out[0] = E and out[1] = eps
+ * (device memory), enqueued on `stream` (NULL = default stream); returns after
+ * the launch.  The paper has no counterpart: this entry point exists for
+ * callers that cannot let the library allocate device memory, such as
+ * real-time loops that must not call cudaMalloc/cudaFree (both can
+ * synchronise the device) or applications whose device memory is reserved by
+ * their own allocator.  It allocates nothing: its scratch, the partial sums of
+ * the reduction, is a fixed 19,456-byte array inside the library that every
+ * device loading the library keeps until the process exits.  The first call on
+ * a device looks up that array's address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  All calls
+ * share the array: calls whose work overlaps on the GPU race and must be
+ * ordered by the caller (one stream, or events).  N must be in [2, 1024];
+ * larger N returns KIN_EINVAL.  nu >= 0.  u and out are the caller's. */
+int kin_energy_dissipation_noalloc(const double* u, int N, double nu, double* out, void* stream);
+
 /* Number of spectrum shells for edge N: 1 + floor(sqrt(3) (N/2) + 1/2). */
 int kin_num_shells(int N);
 

@@ -80,6 +80,7 @@ def _declare(lib):
         "kin_strerror": (ctypes.c_char_p, [c_int]),
         "kin_last_error": (ctypes.c_char_p, []),
         "kin_destroy": (None, [P]),
+        "kin_energy_dissipation_noalloc": (c_int, [P, c_int, c_double, P, P]),
         "kin_ensemble_create": (c_int, [P, c_int, P]),
         "kin_ensemble_set_tuning": (c_int, [P, c_int, c_int, c_int]),
         "kin_ensemble_step": (c_int, [P, c_int]),
@@ -137,6 +138,14 @@ def footprint_bytes(N: int, scheme: int, storage: int) -> int:
 
 def num_shells(N: int) -> int:
     return int(lib().kin_num_shells(N))
+
+
+def energy_dissipation_noalloc(u_ptr: int, N: int, nu: float, out_ptr: int, stream=None):
+    """E and eps of a device velocity field u[3][N^3] (FP64) into the device
+    array out[2], without any device allocation (see kin.h)."""
+    _check(lib().kin_energy_dissipation_noalloc(ctypes.c_void_p(u_ptr), int(N), float(nu),
+                                                 ctypes.c_void_p(out_ptr), _stream_handle(stream)),
+           "kin_energy_dissipation_noalloc")
 
 
 def _stream_handle(stream):

@@ -7,10 +7,14 @@
 //   shell_final_kernel     fixed-order sum over blocks
 // Every reduction runs in a fixed order for a given N, so results are
 // bitwise reproducible.
+#include "kin.h"
 #include "kin_common.cuh"
 #include "kin_internal.h"
+#include "kin_sim.h"
 
 #include <cufft.h>
+
+#include <mutex>
 
 namespace kin {
 
@@ -375,3 +379,70 @@ cudaError_t scan_nonfinite(const double* v, size_t n, int* flag, cudaStream_t st
 }
 
 }  // namespace kin
+
+// ---------------------------------------------------------------------------
+// E / eps reduction that allocates nothing.
+//
+// Some callers cannot let the library allocate device memory: a real-time
+// loop must not call cudaMalloc or cudaFree (either can synchronise the whole
+// device), and an application may have reserved all device memory for its own
+// allocator (a framework's caching allocator, a fixed arena).  For them the
+// per-block partial sums of the reduction live in this fixed array compiled
+// into the library instead of in memory allocated per simulation.  It holds
+// 2 x 1216 doubles (19,456 bytes) and exists on every device that loads the
+// library until the process exits.  Every call shares it and overwrites the
+// partials it uses before reading them (nothing has to start at zero); calls
+// whose kernels overlap on the GPU race on it.
+namespace {
+
+constexpr int kNoallocMaxBlocks = 1216;
+constexpr int kNoallocMaxN = 1024;
+static_assert(kNoallocMaxBlocks >= 1216, "partials must cover stats_blocks() for every N");
+
+static __device__ __align__(256) double g_noalloc_partials[2 * kNoallocMaxBlocks];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[128] = {};  // device address of the array, per device ordinal
+
+// Device address of the array on `dev` (the current device), looked up once.
+double* noalloc_scratch(int dev, cudaError_t* err) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (dev < 0 || dev >= 128) {
+        *err = cudaErrorInvalidDevice;
+        return nullptr;
+    }
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        *err = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (*err != cudaSuccess) return nullptr;
+        g_noalloc_ptr[dev] = (double*)p;
+    }
+    *err = cudaSuccess;
+    return g_noalloc_ptr[dev];
+}
+
+}  // namespace
+
+extern "C" int kin_energy_dissipation_noalloc(const double* u, int N, double nu, double* out,
+                                              void* stream) {
+    using namespace kin;
+    if (!u || !out) return set_error(KIN_EINVAL, "NULL device pointer");
+    if (N < 2 || N > kNoallocMaxN)
+        return set_error(KIN_EINVAL,
+                         "N = %d outside [2, %d], the sizes the fixed scratch of this entry point covers",
+                         N, kNoallocMaxN);
+    if (!(nu >= 0.0)) return set_error(KIN_EINVAL, "nu must be >= 0");
+    const int nb = stats_blocks(N);
+    if (nb > kNoallocMaxBlocks)
+        return set_error(KIN_EINVAL, "reduction needs %d blocks, fixed scratch holds %d", nb,
+                         kNoallocMaxBlocks);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_error(KIN_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    double* partials = noalloc_scratch(dev, &e);
+    if (!partials) return set_error(KIN_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    e = energy_dissipation(u, N, nu, partials, out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return set_error(KIN_ECUDA, "reduction launch: %s", cudaGetErrorString(e));
+    return KIN_OK;
+}
+
