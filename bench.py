@@ -53,6 +53,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-stability", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the ensemble, serving and reduced-precision reports")
+    p.add_argument("--serving-seconds", type=float, default=15.0)
     return p.parse_args()
 
 
@@ -126,6 +129,32 @@ def _dist():
     return world, rank, local
 
 
+def bench_config(N: int, storage: str, world: int) -> dict:
+    bpc = BYTES_PER_CELL[storage]
+    return {"workload": "DHIT %d^3 D3Q19: one MRT-LBE step (dt=1) + one DUGKS step (dt=0.5) "
+                        "per bench step; k0=8, Ma=0.15, Re_lambda=70; E, eps every %d steps, "
+                        "E(k) every %d" % (N, STATS_EVERY, SPECTRUM_EVERY),
+            "N": N, "storage": storage,
+            "l2": "inputs larger than L2 (one copy of f is %.2f GB), no flush" % (N ** 3 * bpc / 2 / 1e9),
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """Largest `value` over all ranks (identity without a process group)."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(cells_per_rank: int, steps: int, world: int, tmax: float) -> float:
+    """Cell updates of all ranks over the slowest rank's time (weak scaling)."""
+    return world * cells_per_rank * steps / tmax / 1e6
+
+
 def cpu_baseline_sample(seconds_target: float = 15.0):
     """Time the FP64 oracle (as it stands) on a 128^3 box of the same recipe:
     one LBE and one DUGKS step, repeated while under the time budget."""
@@ -152,6 +181,25 @@ def cpu_baseline_sample(seconds_target: float = 15.0):
             "kind": "oracle",
             "sample": "%d x (one MRT-LBE + one DUGKS step) on a %d^3 box of the same recipe "
                       "(k0=8, Ma=0.15), FP64, %.1f s" % (reps, n, dt)}
+
+
+def extras(args) -> dict:
+    """Batched ensemble, serving and reduced-precision reports (one GPU)."""
+    from paper_1601_03815_gb300 import ensemble as ens_mod
+    from paper_1601_03815_gb300 import precision as prec_mod
+    from paper_1601_03815_gb300 import serving as srv_mod
+
+    out = {}
+    out["ensemble"] = ens_mod.measure(steps=500)
+    reqs = srv_mod.poisson_requests(4.0, args.serving_seconds, seed=2024)
+    backend = srv_mod.GpuBackend()
+    _, rep = srv_mod.Server(backend, 64 * 2 ** 30, 64, 50).run(reqs)
+    backend.close()
+    rep["arrival_window_s"] = args.serving_seconds
+    rep["rate_per_s"] = 4.0
+    out["serving"] = rep
+    out["precision"] = prec_mod.study(args.N, 1000)
+    return out
 
 
 def run_reference(args):
@@ -191,12 +239,12 @@ def run_reference(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * elapsed / max(1, args.steps), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "DHIT D3Q19, one MRT-LBE + one DUGKS step per bench step, "
-                               "k0=8, Ma=0.15, Re_lambda=70; oracle sample box %d^3" % n,
-                   "N": n, "storage": "f64"},
+        "config": bench_config(args.N, args.storage, world),
         "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": oracle.num_threads(),
                          "kind": "oracle",
-                         "sample": "%d^3 box of the 256^3 recipe per step, %d steps" % (n, args.steps)},
+                         "sample": "each bench step: one MRT-LBE + one DUGKS oracle step (FP64) on a "
+                                   "%d^3 box of the same recipe (k0=%g, Ma=0.15, Re_lambda=70), %d steps"
+                                   % (n, min(K0, n / 4), args.steps)},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -274,14 +322,11 @@ def run_ours(args):
     launches = lbe.kernel_launches + dug.kernel_launches - launches0
     t_lbe = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps / 1000.0
     t_dug = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps / 1000.0
-    tmax = elapsed
+    tmax = max_over_ranks(elapsed, dist, "cuda")
     if dist:
-        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax = float(t.item())
         dist.barrier()
     cells = N ** 3
-    value = world * 2 * cells * args.steps / tmax / 1e6
+    value = whole_job_mlups(2 * cells, args.steps, world, tmax)
 
     # end to end through the C ABI: the initial field from pinned host memory,
     # then per step one step of each scheme and a read-back of E and eps
@@ -306,12 +351,8 @@ def run_ours(args):
             lbe.stats()
             dug.stats()
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([te], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": world * 2 * cells * k_e2e / te / 1e6, "unit": "MLUPS",
+        te = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+        e2e = {"value": whole_job_mlups(2 * cells, k_e2e, world, te), "unit": "MLUPS",
                "h2d_bytes_per_step": int(2 * u0.nbytes / k_e2e), "d2h_bytes_per_step": 2 * 2 * 8,
                "steps": k_e2e,
                "what": "kin_set_velocity from pinned host memory for both schemes, then per step "
@@ -351,13 +392,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tmax / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
         "data": "synthetic",
-        "config": {"workload": "DHIT %d^3 D3Q19: one MRT-LBE step (dt=1) + one DUGKS step (dt=0.5) "
-                               "per bench step; k0=8, Ma=0.15, Re_lambda=70; E, eps every %d steps, "
-                               "E(k) every %d" % (N, STATS_EVERY, SPECTRUM_EVERY),
-                   "N": N, "storage": args.storage,
-                   "l2": "inputs larger than L2 (one copy of f is %.2f GB), no flush"
-                         % (cells * bpc / 2 / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": bench_config(N, args.storage, world),
         "per_scheme": per,
         "roofline": {"bound": "hbm", "kernel": "%s step" % dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
@@ -371,6 +406,8 @@ def run_ours(args):
     }
     for sim in (lbe, dug):
         sim.close()
+    if world == 1 and not args.no_extras:
+        line.update(extras(args))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample()
     elif rank == 0:

@@ -6,6 +6,8 @@ file starts with a header naming the case and this command.
   python tests/golden/make_oracle_histories.py lbe256      # ~10 min on 8 cores
   python tests/golden/make_oracle_histories.py c2 lbe      # 128^3, 2000 steps
   python tests/golden/make_oracle_histories.py c2 dugks    # 128^3, 2000 steps (~1.5 h)
+  python tests/golden/make_oracle_histories.py c3 lbe      # 64^3, 1000 steps
+  python tests/golden/make_oracle_histories.py c3 dugks    # 64^3, 1000 steps
 
 Cases
   lbe256  256^3, k0 = 8, Ma = 0.15, Re_lambda = 70, seed 1300: MRT-LBE E and
@@ -14,6 +16,9 @@ Cases
   c2      128^3, k0 = 8, Ma = 0.1, Re_lambda = 25, seed 1200, 2000 steps of
           the named scheme (DUGKS dt = 0.5): E and eps every 10 steps, E(k)
           every 200 steps.
+  c3      64^3 version of the 256^3 timing field: k0 = 8, Ma = 0.15,
+          Re_lambda = 70, seed 1300, 1000 steps (DUGKS dt = 0.5), E and eps
+          every 10 steps, E(k) every 200 steps, until non-finite.
 """
 import math
 import os
@@ -55,28 +60,30 @@ def lbe256():
                 fh.flush()
 
 
-def c2(scheme):
-    N, seed, k0, Ma, re, steps = 128, 1200, 8.0, 0.1, 25.0, 2000
+def c2(scheme, case="c2", N=128, seed=1200, k0=8.0, Ma=0.1, re=25.0, steps=2000):
     dt = 1.0 if scheme == "lbe" else 0.5
     u, info = ki.dhit_velocity(N, seed, k0, Ma, return_info=True)
     nu = ki.nu_from_re_lambda(info["u_prime"], info["omega"], re)
     f = oracle.equilibrium_field(u)
     del u
     nsh = 1 + int(math.floor(math.sqrt(3 * (N // 2) ** 2) + 0.5))
-    hist = os.path.join(HERE, "oracle_c2_128_%s.txt" % scheme)
-    spec = os.path.join(HERE, "oracle_c2_128_%s_spectrum.txt" % scheme)
+    hist = os.path.join(HERE, "oracle_%s_%d_%s.txt" % (case, N, scheme))
+    spec = os.path.join(HERE, "oracle_%s_%d_%s_spectrum.txt" % (case, N, scheme))
     t0 = time.time()
     with open(hist, "w") as fh, open(spec, "w") as fs:
         for h in (fh, fs):
-            h.write("# FP64 oracle, %s, 128^3, k0=%g Ma=%g Re_lambda=%g seed=%d nu=%.17g dt=%g\n"
-                    % (scheme, k0, Ma, re, seed, nu, dt))
-            h.write("# written by: python tests/golden/make_oracle_histories.py c2 %s\n" % scheme)
+            h.write("# FP64 oracle, %s, %d^3, k0=%g Ma=%g Re_lambda=%g seed=%d nu=%.17g dt=%g\n"
+                    % (scheme, N, k0, Ma, re, seed, nu, dt))
+            h.write("# written by: python tests/golden/make_oracle_histories.py %s %s\n" % (case, scheme))
         fh.write("# step E eps\n")
         fs.write("# step E(s) for s = 0..%d\n" % (nsh - 1))
         for n in range(steps + 1):
             if n % 10 == 0:
                 _, uu = oracle.macro(f)
                 E, eps = oracle.energy_dissipation(uu, nu)
+                if not (math.isfinite(E) and math.isfinite(eps)):
+                    fh.write("%d nonfinite nonfinite\n" % n)
+                    break
                 fh.write("%d %.17g %.17g\n" % (n, E, eps))
                 fh.flush()
                 if n % 200 == 0:
@@ -94,5 +101,7 @@ if __name__ == "__main__":
         lbe256()
     elif sys.argv[1] == "c2":
         c2(sys.argv[2])
+    elif sys.argv[1] == "c3":
+        c2(sys.argv[2], case="c3", N=64, seed=1300, k0=8.0, Ma=0.15, re=70.0, steps=1000)
     else:
         raise SystemExit(__doc__)
