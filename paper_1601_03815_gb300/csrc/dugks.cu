@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(256)
     const C usq15 = C(1.5) * (jx * jx + jy * jy + jz * jz);
     static_for<0, Q>([&](auto ic) {
         constexpr int I = decltype(ic)::value;
-        fbp[I * plane + c] = k.a * f[I] + k.b * feq_i<I>(drho, jx, jy, jz, usq15);
+        // Eq. 19 with a + b = 1 written so a fixed point stays exact in any precision
+        fbp[I * plane + c] = f[I] + k.b * (feq_i<I>(drho, jx, jy, jz, usq15) - f[I]);
     });
 }
 
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(128)
     for (int i = 0; i < Q; ++i) {
         const C ft = Traits<S>::load(src + (size_t)i * plane + c);
         const C fb = fbp[(size_t)i * plane + c];
-        const C ftp = C(4.0 / 3.0) * fb - C(1.0 / 3.0) * ft;
+        const C ftp = fb + (fb - ft) * C(1.0 / 3.0);  // Eq. 20: 4/3 fbp - 1/3 ft
         Traits<S>::store(dst + (size_t)i * plane + c, ftp - k.dt * G[i]);
     }
 }

@@ -49,7 +49,7 @@ __device__ __forceinline__ void face_flux(const Get& get, const DugksCoef<C>& k,
         constexpr int I = decltype(ic)::value;
         if constexpr (cc(I, A) != 0) {
             const C fe = feq_i<I>(drho, jx, jy, jz, usq15);
-            const C ff = k.c1 * fbar[I] + k.c2 * fe;
+            const C ff = fbar[I] + k.c2 * (fe - fbar[I]);  // Eq. 18, c1 + c2 = 1
             F[I] = cc(I, A) > 0 ? ff : -ff;
         }
     });

@@ -196,7 +196,8 @@ __device__ __forceinline__ void face_from_records(const C (&P)[NREC], const C (&
         if constexpr (cz(I) != 0) s += C(cz(I)) * uz;
         const C w = C(w36(I)) / C(36);
         const C fe = w * (a0 + s * (C(3) + C(4.5) * s));
-        const C ff = k.c1 * (P[K] + M[K]) + k.c2 * fe;
+        const C fb = P[K] + M[K];
+        const C ff = fb + k.c2 * (fe - fb);  // Eq. 18, c1 + c2 = 1
         F[K] = cc(I, A) > 0 ? ff : -ff;
     });
 }
@@ -267,7 +268,8 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
         const int s = slot_of(z);
         static_for<0, Q>([&](auto ic) {
             constexpr int I = decltype(ic)::value;
-            sm.ring[s][I][row][lane] = kc.a * f[I] + kc.b * feq_i<I>(drho, jx, jy, jz, usq15);
+            // Eq. 19 with a + b = 1 written so a fixed point stays exact in any precision
+            sm.ring[s][I][row][lane] = f[I] + kc.b * (feq_i<I>(drho, jx, jy, jz, usq15) - f[I]);
         });
     };
     // Cell view at ring slot s with the tangential differences in MASK.
@@ -394,7 +396,7 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
                     const C ft = raw_value(z - 1, i);
                     const C fb = sm.ring[sp][i][row][lane];
                     Traits<S>::store(dst + i * plane + c,
-                                     C(4.0 / 3.0) * fb - C(1.0 / 3.0) * ft - kc.dt * Dprev[i]);
+                                     fb + (fb - ft) * C(1.0 / 3.0) - kc.dt * Dprev[i]);
                 }
             }
         }
