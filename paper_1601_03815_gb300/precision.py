@@ -50,14 +50,15 @@ def run_history(N, scheme, storage, seed=1300, k0=8.0, Ma=0.15, re_lambda=70.0, 
     return {"hist": hist, "spec": spec, "nonfinite_at": bad, "nu": nu}
 
 
-def errors(run, ref, shell_floor=1e-6):
-    """Max relative errors of E, eps over the checks both runs have, and of the
-    spectrum shells holding more than shell_floor of the peak shell."""
-    common = sorted(set(run["hist"]) & set(ref["hist"]))
+def errors(run, ref, shell_floor=1e-6, upto=None):
+    """Max relative errors of E, eps over the checks both runs have (up to step
+    `upto`), and of the spectrum shells holding more than shell_floor of the
+    peak shell."""
+    common = sorted(n for n in set(run["hist"]) & set(ref["hist"]) if upto is None or n <= upto)
     eE = max((abs(run["hist"][n][0] / ref["hist"][n][0] - 1) for n in common), default=None)
     ee = max((abs(run["hist"][n][1] / ref["hist"][n][1] - 1) for n in common), default=None)
     ek = None
-    for n in sorted(set(run["spec"]) & set(ref["spec"])):
+    for n in sorted(n for n in set(run["spec"]) & set(ref["spec"]) if upto is None or n <= upto):
         a, b = run["spec"][n], ref["spec"][n]
         m = min(len(a), len(b))
         a, b = a[:m], b[:m]
@@ -73,8 +74,13 @@ def study(N=256, steps=1000, seed=1300):
         runs = {k: run_history(N, scheme, st, seed=seed, steps=steps) for k, st in STORAGES.items()}
         ref = runs["f32"]
         res = {"nonfinite_at": {k: r["nonfinite_at"] for k, r in runs.items()}}
+        bad = [r["nonfinite_at"] for r in runs.values() if r["nonfinite_at"] is not None]
+        # a run that blows up is compared only while all runs are smooth: up to
+        # 20 steps before the earliest non-finite check
+        upto = min(bad) - 20 if bad else None
+        res["compared_through_step"] = upto if upto is not None else steps
         for k in ("f16", "bf16"):
-            res["%s_vs_f32" % k] = errors(runs[k], ref)
+            res["%s_vs_f32" % k] = errors(runs[k], ref, upto=upto)
         out[sname] = res
     return {"N": N, "steps": steps, "field": "k0=8, Ma=0.15, Re_lambda=70, seed %d" % seed,
             "schemes": out}
