@@ -142,6 +142,7 @@ int kin_num_shells(int N);
  *   block_x  LBE: threads per block along x (multiple of 32, <= 1024)
  *   tile_y   DUGKS fused kernel: rows per tile, 4 or 8
  *   zchunk   DUGKS fused kernel: planes each thread block marches through
+ *            (default: as many as keep about two thread blocks per SM)
  *   variant  DUGKS: 0 = fused single launch (default), 1 = two launches
  *            (pre-step into scratch, then flux + update)
  * Results do not depend on the launch shape or variant beyond rounding

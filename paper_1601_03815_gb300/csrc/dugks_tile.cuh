@@ -195,7 +195,7 @@ __device__ __forceinline__ void face_from_records(const C (&P)[NREC], const C (&
         if constexpr (cy(I) != 0) s += C(cy(I)) * uy;
         if constexpr (cz(I) != 0) s += C(cz(I)) * uz;
         const C w = C(w36(I)) / C(36);
-        const C fe = w * (a0 + s * (C(3) + C(4.5) * s));
+        const C fe = w * (a0 + C(4.5) * s * s) + lin3w<C>(cx(I) * cx(I) + cy(I) * cy(I) + cz(I) * cz(I)) * s;
         const C fb = P[K] + M[K];
         const C ff = fb + k.c2 * (fe - fb);  // Eq. 18, c1 + c2 = 1
         F[K] = cc(I, A) > 0 ? ff : -ff;

@@ -95,6 +95,20 @@ int valid(const kin_sim* s) {
     return KIN_OK;
 }
 
+// Planes per fused-DUGKS thread block when the caller has not chosen: as long
+// as possible (fewer halo planes re-read) while the grid still has about two
+// blocks per SM.
+int auto_zchunk(const kin_sim* s) {
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device);
+    const long long tiles_xy = (long long)((s->N + 29) / 30) * ((s->N + s->tile_y - 1) / s->tile_y);
+    long long zc = (long long)s->N * tiles_xy / (2LL * nsm);
+    zc = zc / 8 * 8;
+    if (zc < 8) zc = 8;
+    if (zc > s->N) zc = s->N;
+    return (int)zc;
+}
+
 int launch_step(kin_sim* s) {
     const void* src = s->buf[s->cur];
     void* dst = s->buf[s->cur ^ 1];
@@ -104,7 +118,8 @@ int launch_step(kin_sim* s) {
     else if (s->variant == 1)
         e = dugks_step(s->storage, src, dst, s->fbp, s->N, s->nu, s->dt, s->block_dugks, s->stream);
     else
-        e = dugks_step_fused(s->storage, src, dst, s->N, s->nu, s->dt, s->tile_y, s->zchunk, s->stream);
+        e = dugks_step_fused(s->storage, src, dst, s->N, s->nu, s->dt, s->tile_y,
+                             s->zchunk > 0 ? s->zchunk : auto_zchunk(s), s->stream);
     if (e != cudaSuccess) return fail(KIN_ECUDA, "step launch: %s", cudaGetErrorString(e));
     s->launches += kin_step_launches(s);
     s->cur ^= 1;

@@ -82,8 +82,20 @@ struct Traits<__nv_bfloat16> {
 };
 
 // ---------------------------------------------------------------------------
+// Coefficient 3 W_i of the linear term of Eq. 7 for |xi_i|^2 = r2 (1 or 2).
+// Exactly, 2 (3 W_1) + 8 (3 W_7) = 1 makes sum_i xi_i f_eq_i = rho0 u.  In FP32
+// the rounded values fl(1/6), fl(1/12) sum to 1 + 3e-8, which a DUGKS step
+// multiplies into the momentum every step (f-bar-plus = f + b (f_eq - f));
+// so FP32 uses fl(1/12) and the FP32 value 5592405 * 2^-25 for which the sum
+// is exactly 1.  FP64 keeps 1/6 and 1/12.
+template <typename C>
+__host__ __device__ constexpr C lin3w(int r2) {
+    if constexpr (sizeof(C) == 4) return r2 == 1 ? C(5592405.0 / 33554432.0) : C(11184811.0 / 134217728.0);
+    else return r2 == 1 ? C(1.0 / 6.0) : C(1.0 / 12.0);
+}
+
 // Discrete equilibrium of Eq. 7 with rho0 = 1, RT = 1/3:
-//   f_eq_i = W_i [drho + 3 xi.u + 9/2 (xi.u)^2 - 3/2 |u|^2].
+//   f_eq_i = W_i [drho + 9/2 (xi.u)^2 - 3/2 |u|^2] + 3 W_i xi.u.
 template <int I, typename C>
 __device__ __forceinline__ C feq_i(C drho, C ux, C uy, C uz, C usq15) {
     constexpr int X = cx(I), Y = cy(I), Z = cz(I);
@@ -92,7 +104,8 @@ __device__ __forceinline__ C feq_i(C drho, C ux, C uy, C uz, C usq15) {
     if constexpr (Y != 0) xu += C(Y) * uy;
     if constexpr (Z != 0) xu += C(Z) * uz;
     const C w = C(w36(I)) / C(36);
-    return w * (drho + C(3) * xu + C(4.5) * xu * xu - usq15);
+    if constexpr (I == 0) return w * (drho - usq15);
+    else return w * (drho + C(4.5) * xu * xu - usq15) + lin3w<C>(X * X + Y * Y + Z * Z) * xu;
 }
 
 // delta-rho = sum f, rho0 u = sum xi f (Eq. 8), rho0 = 1.

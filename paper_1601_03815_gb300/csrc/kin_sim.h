@@ -24,7 +24,7 @@ struct kin_sim {
     cufftHandle d2z = 0, z2d = 0;
     bool have_d2z = false, have_z2d = false;
     int block_lbe = 0, block_dugks = 0;
-    int tile_y = 8, zchunk = 32, variant = 0;
+    int tile_y = 8, zchunk = 0, variant = 0;  // zchunk 0: chosen per launch
     int64_t launches = 0;  // own kernel launches
 };
 
