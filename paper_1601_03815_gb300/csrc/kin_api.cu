@@ -99,8 +99,7 @@ int valid(const kin_sim* s) {
 // as possible (fewer halo planes re-read) while the grid still has about two
 // blocks per SM.
 int auto_zchunk(const kin_sim* s) {
-    int nsm = 152;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device);
+    const int nsm = s->num_sms;
     const long long tiles_xy = (long long)((s->N + 29) / 30) * ((s->N + s->tile_y - 1) / s->tile_y);
     long long zc = (long long)s->N * tiles_xy / (2LL * nsm);
     zc = zc / 8 * 8;
@@ -178,6 +177,9 @@ int kin_create(int N, int scheme, double nu, double Ma, double dt, int storage, 
     s->Ma = Ma;
     s->dt = scheme == KIN_LBE_MRT ? 1.0 : dt;
     cudaGetDevice(&s->device);
+    if (cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess ||
+        s->num_sms <= 0)
+        s->num_sms = 152;
     auto bail = [&](int code) {
         kin_destroy(s);
         return code;

@@ -9,6 +9,7 @@ struct kin_sim {
     int N = 0, scheme = 0, storage = 0;
     double nu = 0, Ma = 0, dt = 0;
     int device = 0;
+    int num_sms = 152;  // multiprocessors of `device`, read at creation
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     void* buf[2] = {nullptr, nullptr};

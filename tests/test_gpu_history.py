@@ -6,7 +6,6 @@ seeded input generator.  Tolerance: E(t) and eps(t) within 1e-4 relative over
 the run (FP32 storage against the FP64 oracle); spectrum shells holding more
 than 1e-6 of the peak shell within 1e-3 relative.
 """
-import math
 import os
 
 import numpy as np
