@@ -14,7 +14,7 @@ template <typename C>
 static DugksCoef<C> make_coef(double nu, double dt) {
     const double tau = 3.0 * nu;  // nu = tau RT, RT = 1/3
     const double h = 0.5 * dt;
-    DugksCoef<C> k;
+    DugksCoef<C> k{};
     k.a = C((2.0 * tau - h) / (2.0 * tau + dt));
     k.b = C(3.0 * h / (2.0 * tau + dt));
     k.h = C(h);

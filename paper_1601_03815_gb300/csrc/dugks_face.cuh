@@ -2,6 +2,7 @@
 #pragma once
 
 #include "kin_common.cuh"
+#include "pair_math.cuh"
 
 namespace kin {
 
@@ -11,6 +12,17 @@ namespace kin {
 template <typename C>
 struct DugksCoef {
     C a, b, h, c1, c2, dt;
+    // Derived constants of the fused step (dugks_coef fills them):
+    C hq;            // h / 4, weight of a tangential central difference at a face
+    C qk[2];         // 4.5 c2 W for axis (0) and diagonal (1) velocities
+    C qw[2];         // c2 W
+    C ql[2];         // c2 times the linear-term coefficient 3 W
+    Pr<C> cpp, cpm;  // (1/2 + h, 1/2 - h) and (1/2 - h, 1/2 + h)
+    Pr<C> hqp, hqm;  // (-h/4, h/4) and (h/4, -h/4)
+    Pr<C> b2;        // (b, b)
+    Pr<C> c1p;       // (1 - c2, 1 - c2)
+    Pr<C> third;     // (1/3, 1/3)
+    Pr<C> dts;       // (-dt, dt)
 };
 
 // Interface flux through the face normal to axis A between L (the stencil

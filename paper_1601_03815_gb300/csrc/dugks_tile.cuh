@@ -4,7 +4,8 @@
 // Each CTA owns a 30 x TY column of cells and marches along z through a chunk
 // of planes.  Its 32 x (TY + 2) threads cover the columns plus a one-cell halo;
 // every thread runs the cell pre-step (Eq. 19) of its own column for the next
-// plane into a three-plane ring of f-bar-plus in shared memory.
+// plane into a three-plane ring of f-bar-plus in shared memory, fed by
+// cp.async copies of f-tilde issued two planes ahead.
 //
 // Interface reconstruction splits exactly between the two cells of a face.
 // With G_i^t(X) = fbp_i(X + e_t) - fbp_i(X - e_t) the Eq. 13/15/16 value at the
@@ -12,69 +13,108 @@
 //   fbar_i = P_i^a(L) + M_i^a(R),
 //   P_i^a = (1/2 + h xi_ia) X_i - (h/4) sum_{t != a} xi_it G_i^t,
 //   M_i^a = (1/2 - h xi_ia) X_i - (h/4) sum_{t != a} xi_it G_i^t,
-// where X = fbp at the cell, and the face moments (Eq. 17) split the same way
-// through the moments of X and their tangential differences.  A cell therefore
-// builds a "side record" per axis and sign (the 10 populations with
-// xi_ia != 0 plus density and momentum), and a face flux (Eqs. 18, 10) needs
-// one record from each neighbour: x neighbours exchange records by warp
-// shuffles, y neighbours through shared memory, z neighbours are the same
-// thread one plane apart.
+// where X = fbp at the cell; summed over i, the face moments (Eq. 17) split the
+// same way through the moments of X and their tangential differences.  A cell
+// builds a "side record" per axis and sign (the 5 velocity pairs crossing the
+// face plus density and momentum); a face (Eqs. 17, 7, 18, 10) needs one
+// record from each neighbour: x neighbours exchange records by warp shuffles,
+// y neighbours through shared memory, z neighbours are the same thread one
+// plane apart.  Updates lag one plane so the z face uses one cell view per
+// plane.
+//
+// Opposite populations (2p+1, 2p+2) travel as one pair (pair_math.cuh): both
+// always undergo the same operation with a fixed coefficient pattern, so one
+// packed FP32x2 instruction serves both.  Flux sums are kept sign-folded,
+// Dhat_p = (D_{2p+1}, -D_{2p+2}), so a face adds the same signed value to
+// both members.
 #pragma once
 
-#include "kin_common.cuh"
+#include <type_traits>
+
 #include "dugks_face.cuh"
+#include "kin_common.cuh"
+#include "pair_math.cuh"
 
 namespace kin {
 
-// k-th population (k = 0..9) with xi_iA != 0, in increasing index order.
-__host__ __device__ constexpr int flux_pop(int A, int k) {
-    int n = 0;
-    for (int i = 0; i < Q; ++i)
-        if (cc(i, A) != 0) {
-            if (n == k) return i;
-            ++n;
-        }
-    return -1;
-}
-// Position of population i in the list of axis T, or -1.
-__host__ __device__ constexpr int flux_index(int T, int i) {
-    int n = 0;
-    for (int j = 0; j < Q; ++j)
-        if (cc(j, T) != 0) {
-            if (j == i) return n;
-            ++n;
-        }
-    return -1;
-}
-constexpr int NF = 10;   // populations crossing a face
-constexpr int NREC = 14; // side record: 10 populations + density + 3 momentum
+// ------------------------------------------------------------------ pair tables
+constexpr int NC = 5;  // velocity pairs crossing a face
 
+// Component a of the velocity of pair p (that of population 2p+1).
+__host__ __device__ constexpr int pe(int p, int a) {
+    return a == 0 ? pair_x(p) : a == 1 ? pair_y(p) : pair_z(p);
+}
+// k-th pair (k = 0..4) whose velocity has a nonzero A component.
+__host__ __device__ constexpr int cross_pair(int A, int k) {
+    int n = 0;
+    for (int p = 0; p < NPAIR; ++p)
+        if (pe(p, A) != 0) {
+            if (n == k) return p;
+            ++n;
+        }
+    return -1;
+}
+// Position of pair p in the list of axis A, or -1.
+__host__ __device__ constexpr int cross_index(int A, int p) {
+    int n = 0;
+    for (int q = 0; q < NPAIR; ++q)
+        if (pe(q, A) != 0) {
+            if (q == p) return n;
+            ++n;
+        }
+    return -1;
+}
+// The other nonzero axis of diagonal pair p crossing A (-1 for an axis pair).
+__host__ __device__ constexpr int tang_axis(int p, int A) {
+    for (int t = 0; t < 3; ++t)
+        if (t != A && pe(p, t) != 0) return t;
+    return -1;
+}
+
+// e_p . (x, y, z); the first nonzero component of every e_p is +1.
+template <int P, typename C>
+__device__ __forceinline__ C pdot(C x, C y, C z) {
+    constexpr int X = pair_x(P), Y = pair_y(P), Z = pair_z(P);
+    if constexpr (X != 0) {
+        static_assert(X == 1, "pair velocity convention");
+        if constexpr (Y != 0) return Y > 0 ? x + y : x - y;
+        else if constexpr (Z != 0) return Z > 0 ? x + z : x - z;
+        else return x;
+    } else if constexpr (Y != 0) {
+        static_assert(Y == 1, "pair velocity convention");
+        if constexpr (Z != 0) return Z > 0 ? y + z : y - z;
+        else return y;
+    } else {
+        static_assert(Z == 1, "pair velocity convention");
+        return z;
+    }
+}
+
+// ------------------------------------------------------------------ shared memory
 template <typename C, int TY>
 struct FusedSmem {
-    C ring[3][Q][TY + 2][32];
-    C my[NREC][TY + 2][32];
-    C fy[NF][TY + 1][32];
+    Pr<C> ring[3][NPAIR][TY + 2][32];  // f-bar-plus pairs of planes z - 1, z, z + 1
+    Pr<C> my[NC][TY + 2][32];          // y-face M records (pairs)
+    Pr<C> fy[NC][TY + 1][32];          // y-face values
+    C ring0[3][TY + 2][32];            // rest population of the ring
+    C mym[4][TY + 2][32];              // y-face M records (density, momentum)
 };
 
-// Raw f-tilde staging for 4-byte storage, filled by cp.async: planes z - 1 and
-// z (awaiting their update), z + 1 (next pre-step) and z + 2 (in flight while
+// Raw f-tilde staging for FP32 storage, filled by cp.async: planes z - 1 and z
+// (awaiting their update), z + 1 (next pre-step) and z + 2 (in flight while
 // plane z is computed).  Other storage types read global memory directly.
-template <typename S, int TY>
+template <int TY>
 struct RawStage {
-    S raw[4][Q][TY + 2][32];
+    float2 raw[4][NPAIR][TY + 2][32];
+    float raw0[4][TY + 2][32];
 };
 
 template <typename S>
-constexpr bool kAsyncStage = sizeof(S) == 4;
+constexpr bool kAsyncStage = std::is_same<S, float>::value;
 
-template <typename S>
-__device__ __forceinline__ void cp_async_elem(S* smem_dst, const S* gsrc) {
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    if constexpr (sizeof(S) == 4) {
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
-    } else {
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
-    }
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
@@ -82,124 +122,161 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <typename S, int TY>
 constexpr size_t fused_smem_bytes() {
     using C = typename Traits<S>::C;
-    return sizeof(FusedSmem<C, TY>) + (kAsyncStage<S> ? sizeof(RawStage<S, TY>) : 0);
+    return sizeof(FusedSmem<C, TY>) + (kAsyncStage<S> ? sizeof(RawStage<TY>) : 0);
 }
 
+// ------------------------------------------------------------------ cell view
 template <typename C>
 struct CellView {
-    // tangential differences G[t][k] for population flux_pop(t, k)
-    C G[3][NF];
-    C X[Q];
+    Pr<C> X[NPAIR];   // f-bar-plus pairs at the cell
+    C X0;             // rest population
+    Pr<C> G[3][NC];   // G[t][k] = X(+e_t) - X(-e_t) for pair cross_pair(t, k)
     C drho, j[3], pi[3][3];
-    C DJ[3];     // DJ_t = sum_i xi_it G_i^t
-    C DP[3][3];  // DP[c][t] = sum_i xi_ic xi_it G_i^t
+    C hrho, hj[3];    // drho / 2, j / 2
+    C DJ[3];          // DJ_t = sum_i xi_it G_i^t
+    C DP[3][3];       // DP[c][t] = sum_i xi_ic xi_it G_i^t
 };
 
-// Moments of X (delta-rho, j, Pi) via pair sums.
+// Moments of X (delta-rho, j, Pi = sum xi xi X) via pair sums and differences.
 template <typename C>
-__device__ __forceinline__ void cell_moments(CellView<C>& v) {
+__device__ __forceinline__ void view_moments(CellView<C>& v) {
     C a[NPAIR], b[NPAIR];
 #pragma unroll
     for (int p = 0; p < NPAIR; ++p) {
-        a[p] = v.X[2 * p + 1] + v.X[2 * p + 2];
-        b[p] = v.X[2 * p + 1] - v.X[2 * p + 2];
+        a[p] = v.X[p].x + v.X[p].y;
+        b[p] = v.X[p].x - v.X[p].y;
     }
-    v.drho = v.X[0] + ((a[0] + a[1]) + a[2]) + (((a[3] + a[4]) + (a[5] + a[6])) + (a[7] + a[8]));
+    const C s34 = a[3] + a[4], s56 = a[5] + a[6], s78 = a[7] + a[8];
+    v.drho = v.X0 + (((a[0] + a[1]) + a[2]) + ((s34 + s56) + s78));
     v.j[0] = (b[0] + b[3]) + (b[4] + (b[5] + b[6]));
     v.j[1] = (b[1] + b[3]) - (b[4] - (b[7] + b[8]));
     v.j[2] = (b[2] + b[5]) - (b[6] - (b[7] - b[8]));
-    // Pi_ab = sum xi_a xi_b X: diagonal from pairs with that component, off-diagonal from
-    // the diagonal-velocity pairs (p = 3,4: xy; 5,6: xz; 7,8: yz)
-    v.pi[0][0] = a[0] + ((a[3] + a[4]) + (a[5] + a[6]));
-    v.pi[1][1] = a[1] + ((a[3] + a[4]) + (a[7] + a[8]));
-    v.pi[2][2] = a[2] + ((a[5] + a[6]) + (a[7] + a[8]));
+    v.pi[0][0] = a[0] + (s34 + s56);
+    v.pi[1][1] = a[1] + (s34 + s78);
+    v.pi[2][2] = a[2] + (s56 + s78);
     v.pi[0][1] = v.pi[1][0] = a[3] - a[4];
     v.pi[0][2] = v.pi[2][0] = a[5] - a[6];
     v.pi[1][2] = v.pi[2][1] = a[7] - a[8];
+    v.hrho = C(0.5) * v.drho;
+    v.hj[0] = C(0.5) * v.j[0];
+    v.hj[1] = C(0.5) * v.j[1];
+    v.hj[2] = C(0.5) * v.j[2];
 }
 
-// DJ and DP for the tangential directions T in the mask (bit t set).
+// Coefficient of term k in a difference sum of axis T: W = 3 gives DJ_T
+// (weight e_pT on G.x - G.y), W = c gives DP[c][T] (weight e_pc e_pT on
+// G.x + G.y).
+template <int T, int W>
+__host__ __device__ constexpr int dcoef(int k) {
+    return W == 3 ? pe(cross_pair(T, k), T) : pe(cross_pair(T, k), W) * pe(cross_pair(T, k), T);
+}
+// Signed sum of vals[k] over the nonzero coefficients, starting from the first
+// term (no addition of zero).
+template <int T, int W, int K, bool STARTED, typename C>
+__device__ __forceinline__ C dsum(const C (&vals)[NC], C acc) {
+    if constexpr (K == NC) {
+        return acc;
+    } else {
+        constexpr int cf = dcoef<T, W>(K);
+        if constexpr (cf == 0) {
+            return dsum<T, W, K + 1, STARTED>(vals, acc);
+        } else if constexpr (!STARTED) {
+            return dsum<T, W, K + 1, true>(vals, cf > 0 ? vals[K] : -vals[K]);
+        } else {
+            return dsum<T, W, K + 1, true>(vals, cf > 0 ? acc + vals[K] : acc - vals[K]);
+        }
+    }
+}
+
+// DJ and DP for the tangential directions T in MASK (bit t set).
 template <int MASK, typename C>
-__device__ __forceinline__ void cell_diffs(CellView<C>& v) {
+__device__ __forceinline__ void view_diffs(CellView<C>& v) {
     static_for<0, 3>([&](auto tc) {
         constexpr int T = decltype(tc)::value;
         if constexpr ((MASK >> T) & 1) {
-            C dj = C(0), d[3] = {C(0), C(0), C(0)};
-            static_for<0, NF>([&](auto kc) {
-                constexpr int K = decltype(kc)::value;
-                constexpr int I = flux_pop(T, K);
-                const C g = v.G[T][K];
-                if constexpr (cc(I, T) > 0) {
-                    dj += g;
-                } else {
-                    dj -= g;
-                }
-                d[T] += g;  // xi_it^2 = 1
-                static_for<0, 3>([&](auto ccn) {
-                    constexpr int CC = decltype(ccn)::value;
-                    if constexpr (CC != T && cc(I, CC) != 0) {
-                        if constexpr (cc(I, CC) * cc(I, T) > 0) d[CC] += g;
-                        else d[CC] -= g;
-                    }
-                });
-            });
-            v.DJ[T] = dj;
-            v.DP[0][T] = d[0];
-            v.DP[1][T] = d[1];
-            v.DP[2][T] = d[2];
+            C sg[NC], dg[NC];
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                sg[k] = v.G[T][k].x + v.G[T][k].y;
+                dg[k] = v.G[T][k].x - v.G[T][k].y;
+            }
+            v.DJ[T] = dsum<T, 3, 0, false>(dg, C(0));
+            v.DP[0][T] = dsum<T, 0, 0, false>(sg, C(0));
+            v.DP[1][T] = dsum<T, 1, 0, false>(sg, C(0));
+            v.DP[2][T] = dsum<T, 2, 0, false>(sg, C(0));
         }
     });
 }
 
-// Side record of a cell for axis A; SIGN = +1 gives P (cell is the left/lower
-// neighbour), -1 gives M (cell is the right/upper neighbour).
-template <int A, int SIGN, typename C>
-__device__ __forceinline__ void side_record(const CellView<C>& v, C h, C hq, C (&rec)[NREC]) {
+// ------------------------------------------------------------------ side records
+template <typename C>
+struct Rec {
+    Pr<C> r[NC];  // pairs crossing the face, in cross_pair order
+    C m[4];       // density, momentum
+};
+
+// P (cell on the lower side of the face along A) and M (upper side) records.
+template <int A, bool WANT_P, bool WANT_M, typename C>
+__device__ __forceinline__ void side_records(const CellView<C>& v, const DugksCoef<C>& k, Rec<C>& P,
+                                             Rec<C>& M) {
     constexpr int T1 = (A + 1) % 3, T2 = (A + 2) % 3;
-    static_for<0, NF>([&](auto kc) {
+    static_for<0, NC>([&](auto kc) {
         constexpr int K = decltype(kc)::value;
-        constexpr int I = flux_pop(A, K);
-        C t = C(0);
-        if constexpr (cc(I, T1) != 0) {
-            constexpr int k1 = flux_index(T1, I);
-            t = cc(I, T1) > 0 ? v.G[T1][k1] : -v.G[T1][k1];
+        constexpr int p = cross_pair(A, K);
+        constexpr int sg = pe(p, A);
+        // (1/2 + h xi_iA) for the two members: P uses cpp when e_pA = +1
+        [[maybe_unused]] const Pr<C> cP = sg > 0 ? k.cpp : k.cpm;
+        [[maybe_unused]] const Pr<C> cM = sg > 0 ? k.cpm : k.cpp;
+        if constexpr (p < 3) {
+            if constexpr (WANT_P) P.r[K] = pmul(cP, v.X[p]);
+            if constexpr (WANT_M) M.r[K] = pmul(cM, v.X[p]);
+        } else {
+            constexpr int T = tang_axis(p, A);
+            constexpr int tau = pe(p, T);
+            // -(h/4) xi_iT G_i^T for both members
+            const Pr<C> ht = pmul(tau > 0 ? k.hqp : k.hqm, v.G[T][cross_index(T, p)]);
+            if constexpr (WANT_P) P.r[K] = pfma(cP, v.X[p], ht);
+            if constexpr (WANT_M) M.r[K] = pfma(cM, v.X[p], ht);
         }
-        if constexpr (cc(I, T2) != 0) {
-            constexpr int k2 = flux_index(T2, I);
-            t += cc(I, T2) > 0 ? v.G[T2][k2] : -v.G[T2][k2];
-        }
-        constexpr int s = SIGN * cc(I, A);  // +1 or -1
-        const C coef = s > 0 ? (C(0.5) + h) : (C(0.5) - h);
-        rec[K] = coef * v.X[I] - hq * t;
     });
-    const C sh = SIGN > 0 ? h : -h;
-    rec[10] = C(0.5) * v.drho + sh * v.j[A] - hq * (v.DJ[T1] + v.DJ[T2]);
+    const C br = fma(-k.hq, v.DJ[T1] + v.DJ[T2], v.hrho);
+    if constexpr (WANT_P) P.m[0] = fma(k.h, v.j[A], br);
+    if constexpr (WANT_M) M.m[0] = fma(-k.h, v.j[A], br);
     static_for<0, 3>([&](auto ccn) {
         constexpr int CC = decltype(ccn)::value;
-        rec[11 + CC] = C(0.5) * v.j[CC] + sh * v.pi[A][CC] - hq * (v.DP[CC][T1] + v.DP[CC][T2]);
+        const C bc = fma(-k.hq, v.DP[CC][T1] + v.DP[CC][T2], v.hj[CC]);
+        if constexpr (WANT_P) P.m[1 + CC] = fma(k.h, v.pi[A][CC], bc);
+        if constexpr (WANT_M) M.m[1 + CC] = fma(-k.h, v.pi[A][CC], bc);
     });
 }
 
-// Face flux F_k = xi_{iA} f_i(x_b, t + h) (Eqs. 17, 7, 18, 10) from the two side records.
+// Face values f_i(x_b, t + h) = c1 fbar_i + c2 f_eq_i (Eqs. 17, 7, 18) of the
+// pairs crossing the face along A, from the two side records.
 template <int A, typename C>
-__device__ __forceinline__ void face_from_records(const C (&P)[NREC], const C (&M)[NREC],
-                                                  const DugksCoef<C>& k, C (&F)[NF]) {
-    const C drho = P[10] + M[10];
-    const C ux = P[11] + M[11], uy = P[12] + M[12], uz = P[13] + M[13];
-    const C a0 = drho - C(1.5) * (ux * ux + uy * uy + uz * uz);
-    static_for<0, NF>([&](auto kc) {
+__device__ __forceinline__ void face_values(const Rec<C>& P, const Rec<C>& M, const DugksCoef<C>& k,
+                                            Pr<C> (&ff)[NC]) {
+    const C rho = P.m[0] + M.m[0];
+    const C ux = P.m[1] + M.m[1], uy = P.m[2] + M.m[2], uz = P.m[3] + M.m[3];
+    const C a0 = fma(C(-1.5), fma(uz, uz, fma(uy, uy, ux * ux)), rho);
+    const C wa_ax = k.qw[0] * a0, wa_dg = k.qw[1] * a0;
+    static_for<0, NC>([&](auto kc) {
         constexpr int K = decltype(kc)::value;
-        constexpr int I = flux_pop(A, K);
-        C s = C(0);
-        if constexpr (cx(I) != 0) s += C(cx(I)) * ux;
-        if constexpr (cy(I) != 0) s += C(cy(I)) * uy;
-        if constexpr (cz(I) != 0) s += C(cz(I)) * uz;
-        const C w = C(w36(I)) / C(36);
-        const C fe = w * (a0 + C(4.5) * s * s) + lin3w<C>(cx(I) * cx(I) + cy(I) * cy(I) + cz(I) * cz(I)) * s;
-        const C fb = P[K] + M[K];
-        const C ff = fb + k.c2 * (fe - fb);  // Eq. 18, c1 + c2 = 1
-        F[K] = cc(I, A) > 0 ? ff : -ff;
+        constexpr int p = cross_pair(A, K);
+        constexpr int cls = p < 3 ? 0 : 1;
+        const C s = pdot<p>(ux, uy, uz);
+        const C q = fma(k.qk[cls] * s, s, cls == 0 ? wa_ax : wa_dg);  // c2 W (a0 + 9/2 s^2)
+        const C l = k.ql[cls] * s;                                   // c2 3W s
+        ff[K] = pfma(k.c1p, padd(P.r[K], M.r[K]), pmk(q + l, q - l));
     });
+}
+
+template <typename C>
+__device__ __forceinline__ Pr<C> pshfl_down1(Pr<C> v) {
+    return pmk(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
+}
+template <typename C>
+__device__ __forceinline__ Pr<C> pshfl_up1(Pr<C> v) {
+    return pmk(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1));
 }
 
 __device__ __forceinline__ int wrapc(int v, int n) {
@@ -207,6 +284,7 @@ __device__ __forceinline__ int wrapc(int v, int n) {
     return v < 0 ? v + n : v;
 }
 
+// ------------------------------------------------------------------ the tile
 // One tile (tile coordinates bx, by, bz) of the fused step, run by a
 // 32 x (TY + 2) thread block with fused_smem_bytes<S, TY>() of dynamic shared
 // memory at smem_raw.  Also called by the persistent ensemble kernel.
@@ -216,8 +294,9 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
                                            const DugksCoef<typename Traits<S>::C>& kc,
                                            unsigned char* smem_raw) {
     using C = typename Traits<S>::C;
+    using P2 = Pr<C>;
     FusedSmem<C, TY>& sm = *reinterpret_cast<FusedSmem<C, TY>*>(smem_raw);
-    RawStage<S, TY>* stage = reinterpret_cast<RawStage<S, TY>*>(smem_raw + sizeof(FusedSmem<C, TY>));
+    RawStage<TY>* stage = reinterpret_cast<RawStage<TY>*>(smem_raw + sizeof(FusedSmem<C, TY>));
 
     const int lane = threadIdx.x, row = threadIdx.y;
     const int x0 = bx * 30, y0 = by * TY, z0 = bz * zchunk;
@@ -231,201 +310,280 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
     const size_t plane = (size_t)N * N * N;
     const size_t colidx = (size_t)gx + (size_t)N * gy;
     const size_t nn = (size_t)N * N;
-    const C h = kc.h, hq = C(0.25) * kc.h;
     // x neighbours, clamped so the two halo lanes can run the interior code
     // path (their x differences are never used)
     const int lp = min(lane + 1, 31), lm = max(lane - 1, 0);
 
-    // ring slots hold fbp of planes z-1, z, z+1; raw slots hold f-tilde of
-    // planes z-1 (update), z (next update), z+1 (next pre-step), z+2 (in flight)
-    auto slot_of = [&](int z) { return (z - z0 + 3) % 3; };
+    auto zwrap = [&](int z) { return z < 0 ? z + N : (z >= N ? z - N : z); };
     auto rslot_of = [&](int z) { return (z - z0 + 4) & 3; };
 
     auto issue_plane = [&](int z) {
         if constexpr (kAsyncStage<S>) {
-            const S* p = src + (size_t)wrapc(z, N) * nn + colidx;
+            const S* p = src + (size_t)zwrap(z) * nn + colidx;
             const int s = rslot_of(z);
+            cp_async4(&stage->raw0[s][row][lane], p);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) cp_async_elem(&stage->raw[s][i][row][lane], p + i * plane);
+            for (int q = 0; q < NPAIR; ++q) {
+                cp_async4(&stage->raw[s][q][row][lane].x, p + (2 * q + 1) * plane);
+                cp_async4(&stage->raw[s][q][row][lane].y, p + (2 * q + 2) * plane);
+            }
             cp_async_commit();
         }
     };
-    auto raw_value = [&](int z, int i) -> C {
+    auto raw_pair = [&](int z, int q) -> P2 {
         if constexpr (kAsyncStage<S>) {
-            return (C)stage->raw[rslot_of(z)][i][row][lane];
+            return stage->raw[rslot_of(z)][q][row][lane];
         } else {
-            return Traits<S>::load(src + (size_t)wrapc(z, N) * nn + colidx + i * plane);
+            const S* p = src + (size_t)zwrap(z) * nn + colidx;
+            return pmk(Traits<S>::load(p + (2 * q + 1) * plane), Traits<S>::load(p + (2 * q + 2) * plane));
         }
     };
-    // Eq. 19 for this thread's column at plane z into the ring.
-    auto prestep = [&](int z) {
-        C f[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) f[i] = raw_value(z, i);
-        C drho, jx, jy, jz;
-        moments(f, drho, jx, jy, jz);
-        const C usq15 = C(1.5) * (jx * jx + jy * jy + jz * jz);
-        const int s = slot_of(z);
-        static_for<0, Q>([&](auto ic) {
-            constexpr int I = decltype(ic)::value;
-            // Eq. 19 with a + b = 1 written so a fixed point stays exact in any precision
-            sm.ring[s][I][row][lane] = f[I] + kc.b * (feq_i<I>(drho, jx, jy, jz, usq15) - f[I]);
-        });
+    auto raw_rest = [&](int z) -> C {
+        if constexpr (kAsyncStage<S>) {
+            return stage->raw0[rslot_of(z)][row][lane];
+        } else {
+            return Traits<S>::load(src + (size_t)zwrap(z) * nn + colidx);
+        }
     };
-    // Cell view at ring slot s with the tangential differences in MASK.
-    auto gather = [&](int s, int sm1, int sp1, auto maskc, CellView<C>& v) {
+
+    // Eq. 19 for this thread's column at plane z into ring slot s:
+    // fbp = f + b (f_eq - f), f_eq of a pair = q +/- l (Eq. 7).
+    auto prestep = [&](int z, int s) {
+        P2 f[NPAIR];
+#pragma unroll
+        for (int q = 0; q < NPAIR; ++q) f[q] = raw_pair(z, q);
+        const C f0 = raw_rest(z);
+        C a[NPAIR], b[NPAIR];
+#pragma unroll
+        for (int q = 0; q < NPAIR; ++q) {
+            a[q] = f[q].x + f[q].y;
+            b[q] = f[q].x - f[q].y;
+        }
+        const C drho = f0 + (((a[0] + a[1]) + a[2]) + (((a[3] + a[4]) + (a[5] + a[6])) + (a[7] + a[8])));
+        const C jx = (b[0] + b[3]) + (b[4] + (b[5] + b[6]));
+        const C jy = (b[1] + b[3]) - (b[4] - (b[7] + b[8]));
+        const C jz = (b[2] + b[5]) - (b[6] - (b[7] - b[8]));
+        const C a0 = fma(C(-1.5), fma(jz, jz, fma(jy, jy, jx * jx)), drho);
+        const C wa_ax = (C(2) / C(36)) * a0, wa_dg = (C(1) / C(36)) * a0;
+        static_for<0, NPAIR>([&](auto pc) {
+            constexpr int PP = decltype(pc)::value;
+            constexpr bool AX = PP < 3;
+            const C sd = pdot<PP>(jx, jy, jz);
+            // W (a0 + 9/2 s^2) with 9/2 W = 1/4 (axis) or 1/8 (diagonal)
+            const C q = fma(C(AX ? 0.25 : 0.125) * sd, sd, AX ? wa_ax : wa_dg);
+            const C l = lin3w<C>(AX ? 1 : 2) * sd;
+            sm.ring[s][PP][row][lane] = pfma(kc.b2, psub(pmk(q + l, q - l), f[PP]), f[PP]);
+        });
+        sm.ring0[s][row][lane] = fma(kc.b, (C(12) / C(36)) * a0 - f0, f0);
+    };
+
+    // Cell view at ring slot s0 with the tangential differences in MASK.
+    auto gather = [&](int s0, int sm1, int sp1, auto maskc, CellView<C>& v) {
         constexpr int MASK = decltype(maskc)::value;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) v.X[i] = sm.ring[s][i][row][lane];
+        for (int q = 0; q < NPAIR; ++q) v.X[q] = sm.ring[s0][q][row][lane];
+        v.X0 = sm.ring0[s0][row][lane];
         static_for<0, 3>([&](auto tc) {
             constexpr int T = decltype(tc)::value;
             if constexpr ((MASK >> T) & 1) {
-                static_for<0, NF>([&](auto kc2) {
+                static_for<0, NC>([&](auto kc2) {
                     constexpr int K = decltype(kc2)::value;
-                    constexpr int I = flux_pop(T, K);
-                    C g;
-                    if constexpr (T == 0) g = sm.ring[s][I][row][lp] - sm.ring[s][I][row][lm];
-                    else if constexpr (T == 1) g = sm.ring[s][I][row + 1][lane] - sm.ring[s][I][row - 1][lane];
-                    else g = sm.ring[sp1][I][row][lane] - sm.ring[sm1][I][row][lane];
-                    v.G[T][K] = g;
+                    constexpr int p = cross_pair(T, K);
+                    if constexpr (T == 0) {
+                        v.G[0][K] = psub(sm.ring[s0][p][row][lp], sm.ring[s0][p][row][lm]);
+                    } else if constexpr (T == 1) {
+                        v.G[1][K] = psub(sm.ring[s0][p][row + 1][lane], sm.ring[s0][p][row - 1][lane]);
+                    } else {
+                        v.G[2][K] = psub(sm.ring[sp1][p][row][lane], sm.ring[sm1][p][row][lane]);
+                    }
                 });
             }
         });
-        cell_moments(v);
-        cell_diffs<MASK>(v);
+        view_moments(v);
+        view_diffs<MASK>(v);
     };
+
+    // ring slots of planes z - 1, z, z + 1 (rotated every plane)
+    int s_m1 = 2, s_0 = 0, s_p1 = 1;
 
     issue_plane(z0 - 1);
     issue_plane(z0);
     cp_async_wait_all();
-    prestep(z0 - 1);
-    prestep(z0);
+    prestep(z0 - 1, s_m1);
+    prestep(z0, s_0);
     issue_plane(z0 + 1);
     __syncthreads();
-    C Pz[NREC];   // P^z record of the plane below the current one
-    C Dprev[Q];   // face-flux sum of plane z-1, still missing its +z face
+
+    Rec<C> Pz;        // P^z record of the plane below the current one
+    P2 Dprev[NPAIR];  // sign-folded flux sums of plane z - 1, still missing its +z face
+    P2 Dcur[NPAIR];
+#pragma unroll
+    for (int q = 0; q < NPAIR; ++q) {
+        Dprev[q] = pmk(C(0), C(0));
+        Dcur[q] = pmk(C(0), C(0));
+    }
     if (interior) {
         CellView<C> v;
-        gather(slot_of(z0 - 1), 0, 0, std::integral_constant<int, 3>{}, v);
-        side_record<2, +1>(v, h, hq, Pz);
+        Rec<C> unused;
+        gather(s_m1, s_m1, s_m1, std::integral_constant<int, 3>{}, v);
+        side_records<2, true, false>(v, kc, Pz, unused);
     }
-#pragma unroll
-    for (int i = 0; i < Q; ++i) Dprev[i] = C(0);
 
     for (int z = z0; z <= zend; ++z) {
         const bool last = z == zend;
         if (!last) {
             if constexpr (kAsyncStage<S>) cp_async_wait_all();
-            prestep(z + 1);
+            prestep(z + 1, s_p1);
             if (z + 2 <= zend) issue_plane(z + 2);
         }
         __syncthreads();  // ring slot of z + 1 complete; fy of plane z - 1 complete
-        C Dcur[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) Dcur[i] = C(0);
-        C Py[NREC];
+        Rec<C> Py;
         if (!last) {
-            const int s0 = slot_of(z), sm1 = slot_of(z - 1), sp1 = slot_of(z + 1);
             CellView<C> v;
             // warp-uniform: rows 1..TY take every difference, the halo rows
             // only those their y records need
             if (yin) {
-                gather(s0, sm1, sp1, std::integral_constant<int, 7>{}, v);
+                gather(s_0, s_m1, s_p1, std::integral_constant<int, 7>{}, v);
             } else {
-                gather(s0, sm1, sp1, std::integral_constant<int, 5>{}, v);  // G^x, G^z
+                gather(s_0, s_m1, s_p1, std::integral_constant<int, 5>{}, v);  // G^x, G^z
             }
-            C Px[NREC], Mx[NREC];
             if (yin) {
-                side_record<0, +1>(v, h, hq, Px);
-                side_record<0, -1>(v, h, hq, Mx);
+                // x faces: this lane's face to the right uses the next lane's M record
+                Rec<C> Px, Mx, Mn;
+                side_records<0, true, true>(v, kc, Px, Mx);
+#pragma unroll
+                for (int k = 0; k < NC; ++k) Mn.r[k] = pshfl_down1<C>(Mx.r[k]);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) Mn.m[m] = __shfl_down_sync(0xffffffffu, Mx.m[m], 1);
+                P2 ffx[NC];
+                face_values<0>(Px, Mn, kc, ffx);
+                static_for<0, NC>([&](auto kc2) {
+                    constexpr int K = decltype(kc2)::value;
+                    constexpr int p = cross_pair(0, K);
+                    const P2 fl = pshfl_up1<C>(ffx[K]);
+                    // Dhat = e_px (F(x + 1/2) - F(x - 1/2)), the first contribution
+                    Dcur[p] = pe(p, 0) > 0 ? psub(ffx[K], fl) : psub(fl, ffx[K]);
+                });
             }
             if (xin) {
-                C My[NREC];
-                side_record<1, +1>(v, h, hq, Py);
-                side_record<1, -1>(v, h, hq, My);
+                Rec<C> My;
+                side_records<1, true, true>(v, kc, Py, My);
 #pragma unroll
-                for (int r = 0; r < NREC; ++r) sm.my[r][row][lane] = My[r];
+                for (int k = 0; k < NC; ++k) sm.my[k][row][lane] = My.r[k];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) sm.mym[m][row][lane] = My.m[m];
             }
-            // x faces: this lane's face to the right uses the next lane's M record
-            C Mn[NREC];
-#pragma unroll
-            for (int r = 0; r < NREC; ++r) Mn[r] = __shfl_down_sync(0xffffffffu, Mx[r], 1);
-            C Fx[NF];
-            if (yin && lane <= 30) face_from_records<0>(Px, Mn, kc, Fx);
-            C Fl[NF];
-#pragma unroll
-            for (int r = 0; r < NF; ++r) Fl[r] = __shfl_up_sync(0xffffffffu, Fx[r], 1);
             if (interior) {
-                static_for<0, NF>([&](auto kc2) {
+                // z face (z - 1, z): P^z(z - 1) carried, M^z(z) from this view
+                Rec<C> Pn, Mz;
+                side_records<2, true, true>(v, kc, Pn, Mz);
+                P2 ffz[NC];
+                face_values<2>(Pz, Mz, kc, ffz);
+                static_for<0, NC>([&](auto kc2) {
                     constexpr int K = decltype(kc2)::value;
-                    Dcur[flux_pop(0, K)] += Fx[K] - Fl[K];
+                    constexpr int p = cross_pair(2, K);
+                    constexpr int sg = pe(p, 2);
+                    Dprev[p] = padd_sg<sg>(Dprev[p], ffz[K]);
+                    if constexpr (pe(p, 0) != 0) {
+                        Dcur[p] = padd_sg<-sg>(Dcur[p], ffz[K]);
+                    } else {
+                        Dcur[p] = sg > 0 ? pneg(ffz[K]) : ffz[K];
+                    }
                 });
-                // z face (z-1, z): P^z(z-1) carried, M^z(z) from this view
-                C Mz[NREC], Fz[NF];
-                side_record<2, -1>(v, h, hq, Mz);
-                face_from_records<2>(Pz, Mz, kc, Fz);
-                static_for<0, NF>([&](auto kc2) {
-                    constexpr int K = decltype(kc2)::value;
-                    Dprev[flux_pop(2, K)] += Fz[K];
-                    Dcur[flux_pop(2, K)] -= Fz[K];
-                });
-                side_record<2, +1>(v, h, hq, Pz);
+                Pz = Pn;
             }
         } else if (interior) {
             CellView<C> v;
-            C Mz[NREC], Fz[NF];
-            gather(slot_of(z), 0, 0, std::integral_constant<int, 3>{}, v);
-            side_record<2, -1>(v, h, hq, Mz);
-            face_from_records<2>(Pz, Mz, kc, Fz);
-            static_for<0, NF>([&](auto kc2) {
+            Rec<C> unused, Mz;
+            gather(s_0, s_0, s_0, std::integral_constant<int, 3>{}, v);
+            side_records<2, false, true>(v, kc, unused, Mz);
+            P2 ffz[NC];
+            face_values<2>(Pz, Mz, kc, ffz);
+            static_for<0, NC>([&](auto kc2) {
                 constexpr int K = decltype(kc2)::value;
-                Dprev[flux_pop(2, K)] += Fz[K];
+                constexpr int p = cross_pair(2, K);
+                Dprev[p] = padd_sg<pe(p, 2)>(Dprev[p], ffz[K]);
             });
         }
         // update plane z - 1 (Eqs. 20, 9): its y faces were computed one iteration ago
         if (z > z0 && interior) {
-            static_for<0, NF>([&](auto kc2) {
+            static_for<0, NC>([&](auto kc2) {
                 constexpr int K = decltype(kc2)::value;
-                Dprev[flux_pop(1, K)] += sm.fy[K][row][lane] - sm.fy[K][row - 1][lane];
+                constexpr int p = cross_pair(1, K);
+                constexpr int sg = pe(p, 1);
+                const P2 dy = psub(sm.fy[K][row][lane], sm.fy[K][row - 1][lane]);
+                if constexpr (pe(p, 0) != 0 || pe(p, 2) != 0) {
+                    Dprev[p] = padd_sg<sg>(Dprev[p], dy);
+                } else {
+                    Dprev[p] = sg > 0 ? dy : pneg(dy);
+                }
             });
             if (valid) {
                 const size_t c = (size_t)(z - 1) * nn + colidx;
-                const int sp = slot_of(z - 1);
-#pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    const C ft = raw_value(z - 1, i);
-                    const C fb = sm.ring[sp][i][row][lane];
-                    Traits<S>::store(dst + i * plane + c,
-                                     fb + (fb - ft) * C(1.0 / 3.0) - kc.dt * Dprev[i]);
-                }
+                static_for<0, NPAIR>([&](auto pc) {
+                    constexpr int PP = decltype(pc)::value;
+                    const P2 xb = sm.ring[s_m1][PP][row][lane];
+                    // f-tilde-plus = 4/3 fbp - 1/3 f-tilde (Eq. 20), minus dt times the flux sum (Eq. 9)
+                    const P2 t = pfma(kc.third, psub(xb, raw_pair(z - 1, PP)), xb);
+                    const P2 o = pfma(kc.dts, Dprev[PP], t);
+                    Traits<S>::store(dst + (2 * PP + 1) * plane + c, o.x);
+                    Traits<S>::store(dst + (2 * PP + 2) * plane + c, o.y);
+                });
+                const C xb0 = sm.ring0[s_m1][row][lane];
+                Traits<S>::store(dst + c, fma(C(1.0 / 3.0), xb0 - raw_rest(z - 1), xb0));
             }
         }
         __syncthreads();  // my of plane z complete; fy of plane z - 1 consumed
         if (!last && xin && row <= TY) {
             // y faces of plane z: face r between rows r and r + 1, r = 0..TY
-            C Mu[NREC], Fy[NF];
+            Rec<C> Mu;
 #pragma unroll
-            for (int r = 0; r < NREC; ++r) Mu[r] = sm.my[r][row + 1][lane];
-            face_from_records<1>(Py, Mu, kc, Fy);
+            for (int k = 0; k < NC; ++k) Mu.r[k] = sm.my[k][row + 1][lane];
 #pragma unroll
-            for (int r = 0; r < NF; ++r) sm.fy[r][row][lane] = Fy[r];
+            for (int m = 0; m < 4; ++m) Mu.m[m] = sm.mym[m][row + 1][lane];
+            P2 ffy[NC];
+            face_values<1>(Py, Mu, kc, ffy);
+#pragma unroll
+            for (int k = 0; k < NC; ++k) sm.fy[k][row][lane] = ffy[k];
         }
 #pragma unroll
-        for (int i = 0; i < Q; ++i) Dprev[i] = Dcur[i];
+        for (int q = 0; q < NPAIR; ++q) Dprev[q] = Dcur[q];
+        const int st = s_m1;
+        s_m1 = s_0;
+        s_0 = s_p1;
+        s_p1 = st;
     }
 }
 
-// Coefficients of Eqs. 18-19 for viscosity nu (tau = nu / RT) and step dt.
+// Coefficients of Eqs. 18-19 for viscosity nu (tau = nu / RT) and step dt,
+// with the derived constants of the fused tile.
 template <typename C>
 inline DugksCoef<C> dugks_coef(double nu, double dt) {
     const double tau = 3.0 * nu, h = 0.5 * dt;
-    DugksCoef<C> k;
+    DugksCoef<C> k{};
     k.a = C((2.0 * tau - h) / (2.0 * tau + dt));
     k.b = C(3.0 * h / (2.0 * tau + dt));
     k.h = C(h);
     k.c1 = C(2.0 * tau / (2.0 * tau + h));
     k.c2 = C(h / (2.0 * tau + h));
     k.dt = C(dt);
+    k.hq = C(0.25 * h);
+    const C c2 = k.c2;
+    k.qk[0] = c2 * C(0.25);
+    k.qk[1] = c2 * C(0.125);
+    k.qw[0] = c2 * (C(2) / C(36));
+    k.qw[1] = c2 * (C(1) / C(36));
+    k.ql[0] = c2 * lin3w<C>(1);
+    k.ql[1] = c2 * lin3w<C>(2);
+    k.cpp = pmk(C(0.5 + h), C(0.5 - h));
+    k.cpm = pmk(C(0.5 - h), C(0.5 + h));
+    k.hqp = pmk(-k.hq, k.hq);
+    k.hqm = pmk(k.hq, -k.hq);
+    k.b2 = pmk(k.b, k.b);
+    const C c1 = C(1) - c2;
+    k.c1p = pmk(c1, c1);
+    k.third = pmk(C(1.0 / 3.0), C(1.0 / 3.0));
+    k.dts = pmk(-k.dt, k.dt);
     return k;
 }
 

@@ -35,8 +35,10 @@ def test_result_is_the_same_alone_and_in_the_mix(kin):
 def test_requests_arriving_later_join_running_ones(kin):
     from paper_1601_03815_gb300.serving import GpuBackend, Request, Server
 
-    reqs = [Request(rid=k, N=16, scheme=k % 2, re_lambda=25.0, steps=400, seed=20 + k,
-                    arrival=0.02 * k) for k in range(5)]
+    # the first request runs long enough (1000 ticks) that the later arrivals
+    # find it still resident however fast a tick is
+    reqs = [Request(rid=k, N=16, scheme=k % 2, re_lambda=25.0, steps=20000 if k == 0 else 400,
+                    seed=20 + k, arrival=0.01 * k) for k in range(5)]
     be = GpuBackend()
     res, rep = Server(be, hbm_budget=2 ** 31, max_active=8, chunk=20).run(reqs)
     be.close()
