@@ -112,6 +112,23 @@ struct RawStage {
 template <typename S>
 constexpr bool kAsyncStage = std::is_same<S, float>::value;
 
+// Raw staging of 2-byte storage (FP16, BF16) for even N: lanes 0..16 of a
+// row's warp copy the row of each population as 17 aligned 4-byte words, the
+// 34 elements from x0 - 2; thread `lane` reads element lane + 1.  Odd N (a
+// word would straddle the periodic wrap) reads global memory directly.
+template <typename S, int TY>
+struct RawStage16 {
+    S raw[4][Q][TY + 2][34];
+};
+template <typename S>
+constexpr bool kStage16 = sizeof(S) == 2;
+
+template <typename S>
+__device__ __forceinline__ float to_float(S v) {
+    if constexpr (std::is_same<S, __half>::value) return __half2float(v);
+    else return __bfloat162float(v);
+}
+
 __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
@@ -122,7 +139,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <typename S, int TY>
 constexpr size_t fused_smem_bytes() {
     using C = typename Traits<S>::C;
-    return sizeof(FusedSmem<C, TY>) + (kAsyncStage<S> ? sizeof(RawStage<TY>) : 0);
+    return sizeof(FusedSmem<C, TY>) +
+           (kAsyncStage<S> ? sizeof(RawStage<TY>) : kStage16<S> ? sizeof(RawStage16<S, TY>) : 0);
 }
 
 // ------------------------------------------------------------------ cell view
@@ -297,6 +315,7 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
     using P2 = Pr<C>;
     FusedSmem<C, TY>& sm = *reinterpret_cast<FusedSmem<C, TY>*>(smem_raw);
     RawStage<TY>* stage = reinterpret_cast<RawStage<TY>*>(smem_raw + sizeof(FusedSmem<C, TY>));
+    RawStage16<S, TY>* stage16 = reinterpret_cast<RawStage16<S, TY>*>(smem_raw + sizeof(FusedSmem<C, TY>));
 
     const int lane = threadIdx.x, row = threadIdx.y;
     const int x0 = bx * 30, y0 = by * TY, z0 = bz * zchunk;
@@ -317,7 +336,23 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
     auto zwrap = [&](int z) { return z < 0 ? z + N : (z >= N ? z - N : z); };
     auto rslot_of = [&](int z) { return (z - z0 + 4) & 3; };
 
+    // 2-byte staging: this lane's word starts at element x0 - 2 + 2 lane (even,
+    // so it never straddles the wrap when N is even)
+    const bool use16 = kStage16<S> && (N % 2 == 0);
+    const size_t rowidx = (size_t)N * gy + (size_t)wrapc(x0 - 2 + 2 * lane, N);
+
     auto issue_plane = [&](int z) {
+        if constexpr (kStage16<S>) {
+            if (use16) {
+                if (lane <= 16) {
+                    const S* p = src + (size_t)zwrap(z) * nn + rowidx;
+                    const int s = rslot_of(z);
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) cp_async4(&stage16->raw[s][i][row][2 * lane], p + i * plane);
+                }
+                cp_async_commit();
+            }
+        }
         if constexpr (kAsyncStage<S>) {
             const S* p = src + (size_t)zwrap(z) * nn + colidx;
             const int s = rslot_of(z);
@@ -334,6 +369,13 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
         if constexpr (kAsyncStage<S>) {
             return stage->raw[rslot_of(z)][q][row][lane];
         } else {
+            if constexpr (kStage16<S>) {
+                if (use16) {
+                    const int s = rslot_of(z);
+                    return pmk(to_float(stage16->raw[s][2 * q + 1][row][lane + 1]),
+                               to_float(stage16->raw[s][2 * q + 2][row][lane + 1]));
+                }
+            }
             const S* p = src + (size_t)zwrap(z) * nn + colidx;
             return pmk(Traits<S>::load(p + (2 * q + 1) * plane), Traits<S>::load(p + (2 * q + 2) * plane));
         }
@@ -342,6 +384,9 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
         if constexpr (kAsyncStage<S>) {
             return stage->raw0[rslot_of(z)][row][lane];
         } else {
+            if constexpr (kStage16<S>) {
+                if (use16) return to_float(stage16->raw[rslot_of(z)][0][row][lane + 1]);
+            }
             return Traits<S>::load(src + (size_t)zwrap(z) * nn + colidx);
         }
     };
@@ -406,9 +451,16 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
     // ring slots of planes z - 1, z, z + 1 (rotated every plane)
     int s_m1 = 2, s_0 = 0, s_p1 = 1;
 
+    // wait for this thread's copies; 2-byte rows were copied by other lanes of
+    // the same warp
+    auto wait_copies = [&]() {
+        cp_async_wait_all();
+        if constexpr (kStage16<S>) __syncwarp();
+    };
+
     issue_plane(z0 - 1);
     issue_plane(z0);
-    cp_async_wait_all();
+    wait_copies();
     prestep(z0 - 1, s_m1);
     prestep(z0, s_0);
     issue_plane(z0 + 1);
@@ -432,7 +484,7 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
     for (int z = z0; z <= zend; ++z) {
         const bool last = z == zend;
         if (!last) {
-            if constexpr (kAsyncStage<S>) cp_async_wait_all();
+            if constexpr (kAsyncStage<S> || kStage16<S>) wait_copies();
             prestep(z + 1, s_p1);
             if (z + 2 <= zend) issue_plane(z + 2);
         }

@@ -93,11 +93,19 @@ __global__ void __launch_bounds__(32 * (TY + 2), 1)
             const int N = M.N;
             if (M.scheme == KIN_LBE_MRT) {
                 const size_t plane = (size_t)N * N * N;
-                const long long c0 = (long long)item.y * M.lbe_nodes;
-                const long long c1 = min(c0 + (long long)M.lbe_nodes, (long long)plane);
-                for (long long c = c0 + tid; c < c1; c += NT) {
-                    const int x = (int)(c % N), y = (int)((c / N) % N), z = (int)(c / ((long long)N * N));
-                    lbe_node<float, true>(src, dst, N, plane, x, y, z, M.rates);
+                // N <= 1024, so node indices fit in 32 bits
+                const int c0 = item.y * M.lbe_nodes;
+                const int c1 = (int)min((long long)c0 + M.lbe_nodes, (long long)plane);
+                const int nn = N * N;
+                for (int c = c0 + tid; c < c1; c += 2 * NT) {
+                    const int za = c / nn, ya = (c - za * nn) / N, xa = c - za * nn - ya * N;
+                    const int cb = c + NT;
+                    if (cb < c1) {
+                        const int zb = cb / nn, yb = (cb - zb * nn) / N, xb = cb - zb * nn - yb * N;
+                        lbe_node2<float, true>(src, dst, N, plane, xa, ya, za, xb, yb, zb, M.rates);
+                    } else {
+                        lbe_node<float, true>(src, dst, N, plane, xa, ya, za, M.rates);
+                    }
                 }
             } else {
                 const int per = M.tiles_x * M.tiles_y;

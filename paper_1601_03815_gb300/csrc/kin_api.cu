@@ -215,6 +215,7 @@ void kin_destroy(kin_sim* s) {
         if (s->buf[k]) cudaFree(s->buf[k]);
     if (s->fbp) cudaFree(s->fbp);
     if (s->u) cudaFree(s->u);
+    if (s->u32) cudaFree(s->u32);
     if (s->uh) cudaFree(s->uh);
     if (s->red) cudaFree(s->red);
     if (s->red_out) cudaFree(s->red_out);
@@ -381,8 +382,16 @@ int kin_stats(kin_sim* s, double* E, double* eps, double* Ek) {
     if (int r = valid(s)) return r;
     DeviceGuard g(s->device);
     if (int r = ensure_u(s)) return r;
-    CK(velocity_field(s->storage, s->buf[s->cur], shifted(s), s->N, s->u, s->stream));
-    CK(energy_dissipation(s->u, s->N, s->nu, s->red, s->red_out, s->stream));
+    if (s->storage == ST_F64) {
+        CK(velocity_field(s->storage, s->buf[s->cur], shifted(s), s->N, s->u, s->stream));
+        CK(energy_dissipation(s->u, s->N, s->nu, s->red, s->red_out, s->stream));
+    } else {
+        // FP32 arithmetic per cell (FP64 on this GPU runs at a small fraction
+        // of the FP32 rate), FP64 sums
+        if (!s->u32) CK(cudaMalloc(&s->u32, sizeof(float) * 3 * ncell(s)));
+        CK(velocity_field32(s->storage, s->buf[s->cur], shifted(s), s->N, s->u32, s->stream));
+        CK(energy_dissipation32(s->u32, s->N, s->nu, s->red, s->red_out, s->stream));
+    }
     s->launches += 3;
     double ed[2];
     CK(cudaMemcpyAsync(ed, s->red_out, sizeof(ed), cudaMemcpyDeviceToHost, s->stream));
@@ -393,6 +402,10 @@ int kin_stats(kin_sim* s, double* E, double* eps, double* Ek) {
         return fail(KIN_ENONFINITE, "non-finite statistics at step %lld", (long long)s->step);
     if (Ek) {
         if (int r = ensure_uh(s)) return r;
+        if (s->storage != ST_F64) {
+            CK(velocity_field(s->storage, s->buf[s->cur], shifted(s), s->N, s->u, s->stream));
+            s->launches += 1;
+        }
         const int N = s->N;
         if (!s->have_d2z) {
             CKFFT(cufftPlan3d(&s->d2z, N, N, N, CUFFT_D2Z));

@@ -39,6 +39,11 @@ cudaError_t velocity_field(int storage, const void* state, bool shifted, int N, 
 // E and eps sums: partials[2 * nblocks] then out[2] = {E, eps} (FP64, fixed
 // order).  nblocks = stats_blocks(N).
 int stats_blocks(int N);
+// FP32 statistics path for storage types computed in FP32 (F32, F16, BF16).
+cudaError_t velocity_field32(int storage, const void* state, bool shifted, int N, float* u,
+                             cudaStream_t stream);
+cudaError_t energy_dissipation32(const float* u, int N, double nu, double* partials, double* out,
+                                 cudaStream_t stream);
 cudaError_t energy_dissipation(const double* u, int N, double nu, double* partials, double* out,
                                cudaStream_t stream);
 

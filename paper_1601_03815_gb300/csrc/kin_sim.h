@@ -18,6 +18,7 @@ struct kin_sim {
     int64_t step = 0;
     // statistics scratch (lazy)
     double* u = nullptr;      // 3 N^3
+    float* u32 = nullptr;     // 3 N^3, the E / eps path of FP32-computed storage
     double2* uh = nullptr;    // 3 N^2 (N/2+1)
     double* red = nullptr;    // block partials
     double* red_out = nullptr;

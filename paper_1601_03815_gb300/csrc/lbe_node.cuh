@@ -28,14 +28,12 @@ inline MrtRates<C> lbe_rates(double nu) {
 // COHERENT selects plain loads (data written earlier in the same launch by
 // other thread blocks, read after an acquire) instead of the read-only path.
 template <typename S, bool COHERENT>
-__device__ __forceinline__ void lbe_node(const S* __restrict__ src, S* __restrict__ dst, int N,
-                                         size_t plane, int x, int y, int z,
-                                         const MrtRates<typename Traits<S>::C>& rates) {
+__device__ __forceinline__ void lbe_gather(const S* __restrict__ src, int N, size_t plane, int x, int y,
+                                           int z, typename Traits<S>::C (&f)[Q]) {
     using C = typename Traits<S>::C;
     const int xo[3] = {wrap_dec(x, N), x, wrap_inc(x, N)};
     const int yo[3] = {wrap_dec(y, N) * N, y * N, wrap_inc(y, N) * N};
     const int zo[3] = {wrap_dec(z, N) * N * N, z * N * N, wrap_inc(z, N) * N * N};
-    C f[Q];
     // source of population i is x - xi_i: offset index 1 - xi
     static_for<0, Q>([&](auto ic) {
         constexpr int I = decltype(ic)::value;
@@ -43,11 +41,43 @@ __device__ __forceinline__ void lbe_node(const S* __restrict__ src, S* __restric
         if constexpr (COHERENT) f[I] = (C)src[(size_t)I * plane + idx];
         else f[I] = Traits<S>::load(src + (size_t)I * plane + idx);
     });
-    C drho, jx, jy, jz;
-    mrt_collide(f, rates, drho, jx, jy, jz);
-    const int c = x + yo[1] + zo[1];
+}
+
+template <typename S>
+__device__ __forceinline__ void lbe_scatter(S* __restrict__ dst, int N, size_t plane, int x, int y, int z,
+                                            const typename Traits<S>::C (&f)[Q]) {
+    const int c = x + N * (y + N * z);  // N <= 1024
 #pragma unroll
     for (int i = 0; i < Q; ++i) Traits<S>::store(dst + (size_t)i * plane + c, f[i]);
+}
+
+template <typename S, bool COHERENT>
+__device__ __forceinline__ void lbe_node(const S* __restrict__ src, S* __restrict__ dst, int N,
+                                         size_t plane, int x, int y, int z,
+                                         const MrtRates<typename Traits<S>::C>& rates) {
+    using C = typename Traits<S>::C;
+    C f[Q];
+    lbe_gather<S, COHERENT>(src, N, plane, x, y, z, f);
+    C drho, jx, jy, jz;
+    mrt_collide(f, rates, drho, jx, jy, jz);
+    lbe_scatter<S>(dst, N, plane, x, y, z, f);
+}
+
+// Two nodes with both gathers issued before either collision, so that a
+// thread keeps twice the loads in flight (used where few warps share an SM).
+template <typename S, bool COHERENT>
+__device__ __forceinline__ void lbe_node2(const S* __restrict__ src, S* __restrict__ dst, int N,
+                                          size_t plane, int xa, int ya, int za, int xb, int yb, int zb,
+                                          const MrtRates<typename Traits<S>::C>& rates) {
+    using C = typename Traits<S>::C;
+    C fa[Q], fb[Q];
+    lbe_gather<S, COHERENT>(src, N, plane, xa, ya, za, fa);
+    lbe_gather<S, COHERENT>(src, N, plane, xb, yb, zb, fb);
+    C drho, jx, jy, jz;
+    mrt_collide(fa, rates, drho, jx, jy, jz);
+    mrt_collide(fb, rates, drho, jx, jy, jz);
+    lbe_scatter<S>(dst, N, plane, xa, ya, za, fa);
+    lbe_scatter<S>(dst, N, plane, xb, yb, zb, fb);
 }
 
 }  // namespace kin

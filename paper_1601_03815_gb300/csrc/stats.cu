@@ -1,7 +1,10 @@
 // Statistics and state conversion kernels.
 //
 //   velocity_kernel        u = sum xi_i f_i (Eq. 8 / Eq. 12), FP64 out
+//   velocity32_kernel      the same in FP32, for storage types computed in FP32
 //   ed_partial_kernel      per-block FP64 sums of |u|^2 and s_ab s_ab
+//   ed32_partial_kernel    the same from FP32 u: per-cell terms in FP32,
+//                          per-thread and block sums in FP64
 //   ed_final_kernel        fixed-order sum of the block partials -> {E, eps}
 //   shell_partial_kernel   per-block shell sums of |u_hat|^2 / 2 (Eq. 27)
 //   shell_final_kernel     fixed-order sum over blocks
@@ -67,6 +70,31 @@ __global__ void velocity_kernel(const S* __restrict__ st, bool shifted, int N, s
     u[c] = jx;
     u[plane + c] = jy;
     u[2 * plane + c] = jz;
+}
+
+// FP32 storage, FP32 arithmetic: u in FP32 (the per-cell sums of 19 terms
+// carry the storage's own rounding; the FP64 path above serves FP64 storage).
+template <typename S>
+__global__ void velocity32_kernel(const S* __restrict__ st, bool shifted, int N, size_t plane,
+                                  float* __restrict__ u) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    float j[3] = {0.0f, 0.0f, 0.0f};
+    static_for<0, Q>([&](auto ic) {
+        constexpr int I = decltype(ic)::value;
+        const float v = (float)Traits<S>::load(st + I * plane + stored_index<I>(x, y, z, N, shifted));
+        if constexpr (cx(I) > 0) j[0] += v;
+        if constexpr (cx(I) < 0) j[0] -= v;
+        if constexpr (cy(I) > 0) j[1] += v;
+        if constexpr (cy(I) < 0) j[1] -= v;
+        if constexpr (cz(I) > 0) j[2] += v;
+        if constexpr (cz(I) < 0) j[2] -= v;
+    });
+    const size_t c = (size_t)x + (size_t)N * (y + (size_t)N * z);
+    u[c] = j[0];
+    u[plane + c] = j[1];
+    u[2 * plane + c] = j[2];
 }
 
 constexpr int RED_THREADS = 256;
@@ -137,16 +165,103 @@ __global__ void __launch_bounds__(RED_THREADS)
     }
 }
 
-__global__ void ed_final_kernel(const double* __restrict__ partial, int nblocks, size_t n, double nu,
-                                double* __restrict__ out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// FP32 counterpart of ed_partial_kernel: block b takes the rows (y, z) =
+// b, b + gridDim.x, ... and its threads the cells of a row; the per-cell
+// |u|^2 and s_ab s_ab are formed in FP32, summed in FP32 over at most 8 rows
+// and then in FP64, in a fixed order.
+__global__ void __launch_bounds__(RED_THREADS)
+    ed32_partial_kernel(const float* __restrict__ u, int N, double* __restrict__ partial) {
+    const size_t n = (size_t)N * N * N;
+    double se = 0.0, ss = 0.0;
+    float fe = 0.0f, fs = 0.0f;
+    int rows_in_chunk = 0;
+    for (int r = blockIdx.x; r < N * N; r += gridDim.x) {
+        if (rows_in_chunk == 8) {
+            se += (double)fe;
+            ss += (double)fs;
+            fe = fs = 0.0f;
+            rows_in_chunk = 0;
+        }
+        ++rows_in_chunk;
+        const int y = r % N, z = r / N;
+        const size_t row = (size_t)N * r;
+        const size_t rows[3][2] = {{row, row},
+                                   {(size_t)N * (wrap_inc(y, N) + (size_t)N * z),
+                                    (size_t)N * (wrap_dec(y, N) + (size_t)N * z)},
+                                   {(size_t)N * (y + (size_t)N * wrap_inc(z, N)),
+                                    (size_t)N * (y + (size_t)N * wrap_dec(z, N))}};
+        for (int x = threadIdx.x; x < N; x += RED_THREADS) {
+            const int xs[3][2] = {{wrap_inc(x, N), wrap_dec(x, N)}, {x, x}, {x, x}};
+            float g[3][3];  // g[a][b] = d u_b / d x_a, central differences
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b)
+                    g[a][b] = 0.5f * (u[b * n + rows[a][0] + xs[a][0]] - u[b * n + rows[a][1] + xs[a][1]]);
+            float s2 = 0.0f;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    const float sab = 0.5f * (g[a][b] + g[b][a]);
+                    s2 += sab * sab;
+                }
+            const float u0 = u[row + x], u1 = u[n + row + x], u2 = u[2 * n + row + x];
+            fe += u0 * u0 + u1 * u1 + u2 * u2;
+            fs += s2;
+        }
+    }
+    se += (double)fe;
+    ss += (double)fs;
+    __shared__ double sh[2][RED_THREADS / 32];
+    se = warp_sum(se);
+    ss = warp_sum(ss);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[0][wid] = se;
+        sh[1][wid] = ss;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < RED_THREADS / 32; ++w) {
+            a += sh[0][w];
+            b += sh[1][w];
+        }
+        partial[2 * blockIdx.x] = a;
+        partial[2 * blockIdx.x + 1] = b;
+    }
+}
+
+// One block of FIN_THREADS: thread t sums partials t, t + FIN_THREADS, ... in
+// order, then the warps and the block reduce in a fixed order.
+constexpr int FIN_THREADS = 256;
+__global__ void __launch_bounds__(FIN_THREADS)
+    ed_final_kernel(const double* __restrict__ partial, int nblocks, size_t n, double nu,
+                    double* __restrict__ out) {
     double a = 0.0, b = 0.0;
-    for (int i = 0; i < nblocks; ++i) {
+    for (int i = threadIdx.x; i < nblocks; i += FIN_THREADS) {
         a += partial[2 * i];
         b += partial[2 * i + 1];
     }
-    out[0] = 0.5 * a / (double)n;
-    out[1] = 2.0 * nu * b / (double)n;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    __shared__ double sh[2][FIN_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[0][wid] = a;
+        sh[1][wid] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int w = 0; w < FIN_THREADS / 32; ++w) {
+            ta += sh[0][w];
+            tb += sh[1][w];
+        }
+        out[0] = 0.5 * ta / (double)n;
+        out[1] = 2.0 * nu * tb / (double)n;
+    }
 }
 
 cudaError_t energy_dissipation(const double* u, int N, double nu, double* partials, double* out,
@@ -155,7 +270,17 @@ cudaError_t energy_dissipation(const double* u, int N, double nu, double* partia
     ed_partial_kernel<<<nb, RED_THREADS, 0, stream>>>(u, N, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    ed_final_kernel<<<1, 32, 0, stream>>>(partials, nb, (size_t)N * N * N, nu, out);
+    ed_final_kernel<<<1, FIN_THREADS, 0, stream>>>(partials, nb, (size_t)N * N * N, nu, out);
+    return cudaGetLastError();
+}
+
+cudaError_t energy_dissipation32(const float* u, int N, double nu, double* partials, double* out,
+                                 cudaStream_t stream) {
+    const int nb = stats_blocks(N);
+    ed32_partial_kernel<<<nb, RED_THREADS, 0, stream>>>(u, N, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ed_final_kernel<<<1, FIN_THREADS, 0, stream>>>(partials, nb, (size_t)N * N * N, nu, out);
     return cudaGetLastError();
 }
 
@@ -184,23 +309,24 @@ __global__ void __launch_bounds__(SPEC_THREADS)
     double* mybins = bins + wid * nshell;
     for (int s = lane; s < nshell; s += 32) mybins[s] = 0.0;
     __syncwarp();
+    __shared__ double xch[SPEC_THREADS];  // lane values for the shell sums
     const int nh = N / 2 + 1;
-    const size_t nmode = (size_t)N * N * nh;
+    const int nmode = N * N * nh;  // < 2^31 for N <= 1024
     // each warp handles consecutive chunks of 32 modes
-    const size_t nwarps = (size_t)gridDim.x * (SPEC_THREADS / 32);
-    const size_t gw = (size_t)blockIdx.x * (SPEC_THREADS / 32) + wid;
-    for (size_t base = gw * 32; base < nmode; base += nwarps * 32) {
-        const size_t m = base + lane;
+    const int nwarps = gridDim.x * (SPEC_THREADS / 32);
+    const int gw = blockIdx.x * (SPEC_THREADS / 32) + wid;
+    for (int base = gw * 32; base < nmode; base += nwarps * 32) {
+        const int m = base + lane;
         int shell = -1;
         double e = 0.0;
         if (m < nmode) {
-            const int kx = (int)(m % nh);
-            const int ky = (int)((m / nh) % N);
-            const int kz = (int)(m / ((size_t)nh * N));
+            const int kx = m % nh, t = m / nh;
+            const int ky = t % N, kz = t / N;
             const int sy = ky > N / 2 ? ky - N : ky;
             const int sz = kz > N / 2 ? kz - N : kz;
-            const long long n2 = (long long)kx * kx + (long long)sy * sy + (long long)sz * sz;
-            shell = (int)floor(sqrt((double)n2) + 0.5);
+            const int n2 = kx * kx + sy * sy + sz * sz;  // < 2^24: exact in FP32
+            // nearest integer to |n|; |n| is never within FP32 rounding of a half-integer
+            shell = (int)floorf(sqrtf((float)n2) + 0.5f);
             const double2 a = u0[m], b = u1[m], c = u2[m];
             const double amp = (a.x * a.x + a.y * a.y) + (b.x * b.x + b.y * b.y) + (c.x * c.x + c.y * c.y);
             const double w = (kx > 0 && 2 * kx < N) ? 2.0 : 1.0;
@@ -209,12 +335,14 @@ __global__ void __launch_bounds__(SPEC_THREADS)
         }
         const unsigned same = __match_any_sync(0xffffffffu, shell);
         const int leader = __ffs(same) - 1;
-        double acc = 0.0;
-        for (int l = 0; l < 32; ++l) {
-            const double v = __shfl_sync(0xffffffffu, e, l);
-            if ((same >> l) & 1u) acc += v;
+        xch[threadIdx.x] = e;
+        __syncwarp();
+        if (lane == leader && shell >= 0 && shell < nshell) {
+            // the lanes of this shell in lane order
+            double acc = 0.0;
+            for (unsigned msk = same; msk; msk &= msk - 1) acc += xch[wid * 32 + __ffs(msk) - 1];
+            mybins[shell] += acc;
         }
-        if (lane == leader && shell >= 0 && shell < nshell) mybins[shell] += acc;
         __syncwarp();
     }
     __syncthreads();
@@ -332,6 +460,22 @@ cudaError_t velocity_field(int storage, const void* state, bool shifted, int N, 
     dim3 g = row_grid(N, bx);
     const size_t plane = (size_t)N * N * N;
     KIN_DISPATCH(storage, (velocity_kernel<S><<<g, bx, 0, stream>>>((const S*)state, shifted, N, plane, u)));
+    return cudaGetLastError();
+}
+
+cudaError_t velocity_field32(int storage, const void* state, bool shifted, int N, float* u,
+                             cudaStream_t stream) {
+    int bx;
+    dim3 g = row_grid(N, bx);
+    const size_t plane = (size_t)N * N * N;
+    switch (storage) {
+        case ST_F32: velocity32_kernel<float><<<g, bx, 0, stream>>>((const float*)state, shifted, N, plane, u); break;
+        case ST_F16: velocity32_kernel<__half><<<g, bx, 0, stream>>>((const __half*)state, shifted, N, plane, u); break;
+        case ST_BF16:
+            velocity32_kernel<__nv_bfloat16><<<g, bx, 0, stream>>>((const __nv_bfloat16*)state, shifted, N, plane, u);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -144,7 +144,7 @@ def test_init_field_matches_input_generator(kin, orc):
             sim.close()
 
 
-@pytest.mark.parametrize("storage", [3, 0])
+@pytest.mark.parametrize("storage", [3, 0, 1, 2])
 def test_stats_match_oracle(kin, orc, storage):
     N = 24
     f0 = _state(orc, N, 3)
@@ -155,7 +155,11 @@ def test_stats_match_oracle(kin, orc, storage):
     Eo, eo = orc.stats(fin, 0.02)
     _, uo = orc.macro(fin)
     Eko, _ = orc.spectrum(uo, kin.num_shells(N))
-    assert abs(E / Eo - 1) < 1e-12 and abs(eps / eo - 1) < 1e-12
+    # FP64 storage is summed in FP64 throughout; the FP32-computed storage
+    # types form each cell's |u|^2 and s_ab s_ab in FP32 (a few roundings of
+    # 6e-8 each) and sum them in FP64
+    tol = 1e-12 if storage == 3 else 2e-6
+    assert abs(E / Eo - 1) < tol and abs(eps / eo - 1) < tol, (E / Eo - 1, eps / eo - 1)
     np.testing.assert_allclose(Ek, Eko, rtol=1e-10, atol=1e-14 * Eko.max())
     # fixed-order reductions: bitwise reproducible
     E2, eps2, Ek2 = sim.stats(spectrum=True)

@@ -19,7 +19,8 @@ def test_noalloc_energy_dissipation_matches_kin_stats(kin):
     import torch
 
     N, nu = 24, 0.02
-    sim = kin.Sim(N, kin.LBE_MRT, nu, 0.1, 1.0, kin.F32)
+    # FP64 storage: kin_stats then sums in FP64 exactly as the no-alloc path does
+    sim = kin.Sim(N, kin.LBE_MRT, nu, 0.1, 1.0, kin.F64)
     sim.init_field(11, 4.0, 0.0)
     E_ref, eps_ref = sim.stats()
     u = torch.from_numpy(sim.get_velocity()).cuda().contiguous()
