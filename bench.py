@@ -386,7 +386,12 @@ def run_ours(args):
     dom = "dugks" if t_dug >= t_lbe else "lbe"
     t_dom = t_dug if dom == "dugks" else t_lbe
     achieved = bpc * cells / t_dom / 1e9
+    # DRAM read + write bytes of one ncu capture of the current fused DUGKS
+    # kernel at 128^3 FP32 (dram__bytes_read.sum + dram__bytes_write.sum =
+    # 170,673,664 + 116,180,992), scaled by the 8x cells of a 256^3 launch
     traffic = None
+    if dom == "dugks" and args.storage == "f32" and N == 256:
+        traffic = (170673664 + 116180992) * 8
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tmax / args.steps,

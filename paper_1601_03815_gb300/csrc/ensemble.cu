@@ -3,14 +3,16 @@
 //
 // The work of one time step is a list of items (member, tile): a DUGKS tile
 // of the fused step (dugks_tile.cuh) or a run of consecutive LBE nodes
-// (lbe_node.cuh).  Every thread block walks the list grid-stride, in the same
-// order at every step.  A member's step s may start only when all its tiles of
-// step s - 1 are done: each finished tile adds one to the member's counter with
-// a GPU-scope release, and a block waits for count >= s * tiles with acquire
-// loads before touching the member.  All blocks are co-resident (cooperative
-// launch), and each block finishes its step s - 1 items before any step s
-// item, so every wait is eventually satisfied; it is nevertheless bounded in
-// time and sets a status word (and releases every other waiter) if it runs out.
+// (lbe_node.cuh).  Thread blocks take (step, item) pairs one at a time from a
+// global counter, all items of step s before any of step s + 1.  A member's
+// step s may start only when all its tiles of step s - 1 are done: each
+// finished tile adds one to the member's counter with a GPU-scope release, and
+// a block waits for count >= s * tiles with acquire loads before touching the
+// member.  All blocks are co-resident (cooperative launch) and every item a
+// wait depends on was handed out earlier to a running block, so every wait is
+// eventually satisfied; it is nevertheless bounded in time and sets a status
+// word (and releases every other waiter) if it runs out.  Which block runs an
+// item does not change what the item computes.
 //
 // Double buffering: step s reads buf[(cur + s) & 1] and writes the other
 // buffer; the member barrier makes every read of step s - 1 precede every
@@ -54,13 +56,24 @@ __device__ __forceinline__ int ld_relaxed(const int* p) {
 template <int TY>
 __global__ void __launch_bounds__(32 * (TY + 2), 1)
     ensemble_kernel(const EnsMember* __restrict__ mem, const int2* __restrict__ items, int nitems,
-                    int nsteps, unsigned* done, int* status, long long wait_cycles, int stall_test) {
+                    int nsteps, unsigned* done, unsigned* next_item, int* status, long long wait_cycles,
+                    int stall_test) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_abort;
+    __shared__ unsigned s_idx;
     const int tid = threadIdx.y * 32 + threadIdx.x;
     constexpr int NT = 32 * (TY + 2);
-    for (int s = 0; s < nsteps; ++s) {
-        for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    // Blocks take (step, item) pairs in order from a global counter: every
+    // item of step s is handed out before any of step s + 1, so an item only
+    // waits on items already running in resident blocks.
+    const unsigned total = (unsigned)nsteps * (unsigned)nitems;
+    for (;;) {
+        if (tid == 0) s_idx = atomicAdd(next_item, 1u);
+        __syncthreads();
+        const unsigned idx = s_idx;
+        if (idx >= total) return;
+        {
+            const int s = (int)(idx / (unsigned)nitems), it = (int)(idx % (unsigned)nitems);
             const int2 item = items[it];
             const EnsMember& M = mem[item.x];
             if (tid == 0) {
@@ -96,16 +109,17 @@ __global__ void __launch_bounds__(32 * (TY + 2), 1)
                 // N <= 1024, so node indices fit in 32 bits
                 const int c0 = item.y * M.lbe_nodes;
                 const int c1 = (int)min((long long)c0 + M.lbe_nodes, (long long)plane);
-                const int nn = N * N;
-                for (int c = c0 + tid; c < c1; c += 2 * NT) {
-                    const int za = c / nn, ya = (c - za * nn) / N, xa = c - za * nn - ya * N;
-                    const int cb = c + NT;
-                    if (cb < c1) {
-                        const int zb = cb / nn, yb = (cb - zb * nn) / N, xb = cb - zb * nn - yb * N;
-                        lbe_node2<float, true>(src, dst, N, plane, xa, ya, za, xb, yb, zb, M.rates);
-                    } else {
-                        lbe_node<float, true>(src, dst, N, plane, xa, ya, za, M.rates);
-                    }
+                constexpr int K = 3;  // nodes per thread in flight
+                int c = c0 + tid;
+                for (; c + (K - 1) * NT < c1; c += K * NT) {
+                    int cs[K];
+#pragma unroll
+                    for (int k = 0; k < K; ++k) cs[k] = c + k * NT;
+                    lbe_nodes<K, float, true>(src, dst, N, plane, cs, M.rates);
+                }
+                for (; c < c1; c += NT) {
+                    const int cs[1] = {c};
+                    lbe_nodes<1, float, true>(src, dst, N, plane, cs, M.rates);
                 }
             } else {
                 const int per = M.tiles_x * M.tiles_y;
@@ -244,10 +258,12 @@ int launch(kin_ensemble* e, int nsteps, int stall_test) {
     cudaError_t err;
     if (e->tile_y == 4)
         err = cudaLaunchKernelEx(&cfg, ensemble_kernel<4>, (const EnsMember*)e->d_mem, (const int2*)e->d_items,
-                                 e->nitems, nsteps, e->d_done, e->d_status, wc, stall_test);
+                                 e->nitems, nsteps, e->d_done, e->d_done + e->members.size(), e->d_status,
+                                 wc, stall_test);
     else
         err = cudaLaunchKernelEx(&cfg, ensemble_kernel<8>, (const EnsMember*)e->d_mem, (const int2*)e->d_items,
-                                 e->nitems, nsteps, e->d_done, e->d_status, wc, stall_test);
+                                 e->nitems, nsteps, e->d_done, e->d_done + e->members.size(), e->d_status,
+                                 wc, stall_test);
     if (err != cudaSuccess) return ens_fail(KIN_ECUDA, "ensemble launch", err);
     return KIN_OK;
 }
@@ -268,7 +284,7 @@ int run(kin_ensemble* e, int nsteps, int stall_test) {
     if (int r = sync_members(e)) return r;
     if (int r = refresh_table(e)) return r;
     if (stall_test) {
-        ECK(cudaMemsetAsync(e->d_done, 0, sizeof(unsigned) * e->members.size(), e->stream));
+        ECK(cudaMemsetAsync(e->d_done, 0, sizeof(unsigned) * (e->members.size() + 1), e->stream));
         ECK(cudaMemsetAsync(e->d_status, 0, sizeof(int), e->stream));
         if (int r = launch(e, nsteps, 1)) return r;
     } else {
@@ -276,7 +292,7 @@ int run(kin_ensemble* e, int nsteps, int stall_test) {
         if (it == e->graphs.end()) {
             cudaGraph_t g = nullptr;
             ECK(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
-            cudaMemsetAsync(e->d_done, 0, sizeof(unsigned) * e->members.size(), e->stream);
+            cudaMemsetAsync(e->d_done, 0, sizeof(unsigned) * (e->members.size() + 1), e->stream);
             cudaMemsetAsync(e->d_status, 0, sizeof(int), e->stream);
             const int rl = launch(e, nsteps, 0);
             cudaError_t ce = cudaStreamEndCapture(e->stream, &g);
@@ -337,7 +353,9 @@ int kin_ensemble_create(kin_sim* const* members, int n, kin_ensemble** out) {
     if ((c = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(ens_fail(KIN_ECUDA, "stream", c));
     if ((c = cudaMalloc(&e->d_mem, sizeof(EnsMember) * n)) != cudaSuccess) return bail(ens_fail(KIN_ENOMEM, "table", c));
-    if ((c = cudaMalloc(&e->d_done, sizeof(unsigned) * n)) != cudaSuccess) return bail(ens_fail(KIN_ENOMEM, "counters", c));
+    // one completion counter per member, then the work counter
+    if ((c = cudaMalloc(&e->d_done, sizeof(unsigned) * (n + 1))) != cudaSuccess)
+        return bail(ens_fail(KIN_ENOMEM, "counters", c));
     if ((c = cudaMalloc(&e->d_status, sizeof(int))) != cudaSuccess) return bail(ens_fail(KIN_ENOMEM, "status", c));
     if (int r = build_tables(e)) return bail(r);
     cudaSetDevice(prev);

@@ -63,21 +63,31 @@ __device__ __forceinline__ void lbe_node(const S* __restrict__ src, S* __restric
     lbe_scatter<S>(dst, N, plane, x, y, z, f);
 }
 
-// Two nodes with both gathers issued before either collision, so that a
-// thread keeps twice the loads in flight (used where few warps share an SM).
-template <typename S, bool COHERENT>
-__device__ __forceinline__ void lbe_node2(const S* __restrict__ src, S* __restrict__ dst, int N,
-                                          size_t plane, int xa, int ya, int za, int xb, int yb, int zb,
+// K nodes (cells c[0..K-1], linear index x + N (y + N z)) with every gather
+// issued before the first collision, so that a thread keeps K times the loads
+// in flight (used where few warps share an SM).
+template <int K, typename S, bool COHERENT>
+__device__ __forceinline__ void lbe_nodes(const S* __restrict__ src, S* __restrict__ dst, int N,
+                                          size_t plane, const int (&c)[K],
                                           const MrtRates<typename Traits<S>::C>& rates) {
     using C = typename Traits<S>::C;
-    C fa[Q], fb[Q];
-    lbe_gather<S, COHERENT>(src, N, plane, xa, ya, za, fa);
-    lbe_gather<S, COHERENT>(src, N, plane, xb, yb, zb, fb);
-    C drho, jx, jy, jz;
-    mrt_collide(fa, rates, drho, jx, jy, jz);
-    mrt_collide(fb, rates, drho, jx, jy, jz);
-    lbe_scatter<S>(dst, N, plane, xa, ya, za, fa);
-    lbe_scatter<S>(dst, N, plane, xb, yb, zb, fb);
+    C f[K][Q];
+    int xyz[K][3];
+    const int nn = N * N;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        xyz[k][2] = c[k] / nn;
+        xyz[k][1] = (c[k] - xyz[k][2] * nn) / N;
+        xyz[k][0] = c[k] - xyz[k][2] * nn - xyz[k][1] * N;
+        lbe_gather<S, COHERENT>(src, N, plane, xyz[k][0], xyz[k][1], xyz[k][2], f[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        C drho, jx, jy, jz;
+        mrt_collide(f[k], rates, drho, jx, jy, jz);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) lbe_scatter<S>(dst, N, plane, xyz[k][0], xyz[k][1], xyz[k][2], f[k]);
 }
 
 }  // namespace kin
