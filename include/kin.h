@@ -113,10 +113,35 @@ int kin_step(kin_sim* sim, int n);
  *          differences of u (grid form of Eq. 26)
  *   Ek   NULL, or kin_num_shells(N) doubles: E(s) = sum over modes with
  *          floor(|n| + 1/2) = s of |u_hat|^2 / 2, u_hat = N^-3 FFT(u) (Eq. 27)
- * Any output pointer may be NULL.  FP64 reductions in a fixed order: the
- * result is bitwise reproducible for a given state.
+ * Any output pointer may be NULL.  Reductions run in a fixed order: the
+ * result is bitwise reproducible for a given state.  FP64 storage is reduced
+ * in FP64 throughout; for FP32, FP16 and BF16 storage E and eps form each
+ * cell's |u|^2 and s_ab s_ab in FP32 and sum them in FP64 (relative error
+ * ~1e-7), and Ek is computed from an FP64 velocity field.
  * Returns KIN_ENONFINITE if E is not finite. */
 int kin_stats(kin_sim* sim, double* E, double* eps, double* Ek);
+
+/* Derived statistics of the current state (Sec. III; synchronises the stream):
+ *   out[0] E          <u.u>/2
+ *   out[1] u'         sqrt(<u.u>/3)
+ *   out[2] eps        spectral dissipation 2 nu sum_k |k|^2 E_k (Eq. 26),
+ *                     k = 2 pi n / N
+ *   out[3] lambda     transverse Taylor microscale sqrt(15 nu / eps) u'
+ *   out[4] Re_lambda  u' lambda / nu
+ *   out[5] eta        Kolmogorov length (nu^3 / eps)^(1/4)
+ *   out[6] S          velocity-derivative skewness
+ *   out[7] F          velocity-derivative flatness
+ *   D   NULL, or kin_num_shells(N) doubles: the dissipation spectrum
+ *       D(s) = 2 nu sum over the modes of shell s of |k|^2 |u_hat|^2 / 2,
+ *       so sum_s D(s) = eps
+ * S = sum_a <(d_a u_a)^3> / sum_a <(d_a u_a)^2>^(3/2) and
+ * F = sum_a <(d_a u_a)^4> / sum_a <(d_a u_a)^2>^2 over a = x, y, z, with
+ * spectral derivatives (i k_a u_hat, the Nyquist wavenumber dropped).  The
+ * printed formulas of S and F carry an extra factor 3 in the denominator,
+ * read as a misprint (it would give a Gaussian field the flatness 1, not 3).
+ * Everything in FP64; uses the statistics scratch and overwrites nothing of
+ * the state.  Returns KIN_ENONFINITE if E is not finite. */
+int kin_derived_stats(kin_sim* sim, double* out, double* D);
 
 /* E and eps (as in kin_stats) of a velocity field u[3][N^3] (FP64, x fastest)
  * that is already in device memory, written to out[0] = E and out[1] = eps

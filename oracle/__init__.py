@@ -258,3 +258,59 @@ def spectrum(u, nshell: int | None = None):
                              + kx[None, None, :] ** 2 / nx ** 2)
     omega = float(np.sum(k2 * e))
     return E, omega
+
+
+def derived_stats(u, nu: float, nshell: int | None = None):
+    """Derived statistics of Sec. III: u', the Taylor microscale lambda,
+    Re_lambda, the Kolmogorov length eta, the dissipation spectrum
+    D(k) = 2 nu k^2 E(k), and the velocity-derivative skewness S and flatness F
+    averaged over the three directions.
+
+    eps is the spectral dissipation 2 nu sum_k |k|^2 E (Eq. 26); D(n) bins the
+    same per-mode terms by shell, so sum_n D(n) = eps.  The derivatives
+    du/dx, dv/dy, dw/dz are spectral (i k u_hat, Nyquist wavenumber dropped),
+    taken with numpy's one-dimensional FFT along their own axis.
+
+    S and F are the direction-summed third and fourth moments over the
+    direction-summed powers of the second moment.  The printed formulas carry
+    an extra factor 3 in the denominator, which would make a Gaussian field's
+    flatness 1 rather than 3; the text calls them the skewness and flatness
+    averaged over the three directions, so the factor is read as spurious.
+    """
+    u = _f64(u)
+    nz, ny, nx = u.shape[1:]
+    ncell = nx * ny * nz
+    uh = np.fft.fftn(u, axes=(1, 2, 3)) / ncell
+    e = 0.5 * np.sum(np.abs(uh) ** 2, axis=0)
+    fz = np.fft.fftfreq(nz, 1.0 / nz)
+    fy = np.fft.fftfreq(ny, 1.0 / ny)
+    fx = np.fft.fftfreq(nx, 1.0 / nx)
+    n2 = fz[:, None, None] ** 2 + fy[None, :, None] ** 2 + fx[None, None, :] ** 2
+    shell = np.floor(np.sqrt(n2) + 0.5).astype(np.int64)
+    if nshell is None:
+        nshell = int(shell.max()) + 1
+    k2 = (2 * np.pi) ** 2 * (fz[:, None, None] ** 2 / nz ** 2 + fy[None, :, None] ** 2 / ny ** 2
+                             + fx[None, None, :] ** 2 / nx ** 2)
+    D = 2.0 * nu * np.bincount(shell.ravel(), weights=(k2 * e).ravel(), minlength=nshell)[:nshell]
+    eps = 2.0 * nu * float(np.sum(k2 * e))
+    uu = float(np.mean(np.sum(u * u, axis=0)))
+    uprime = np.sqrt(uu / 3.0)
+    lam = np.sqrt(15.0 * nu / eps) * uprime
+    m = np.zeros((3, 3))  # m[a][p - 2] = <(d_a u_a)^p>
+    for a, axis in ((0, 3), (1, 2), (2, 1)):
+        n = u.shape[axis]
+        f = np.fft.fftfreq(n, 1.0 / n)
+        k = 2.0 * np.pi * f / n
+        if n % 2 == 0:
+            k[n // 2] = 0.0  # the Nyquist wavenumber has no real derivative
+        shape = [1, 1, 1]
+        shape[axis - 1] = n
+        d = np.real(np.fft.ifft(1j * k.reshape(shape) * np.fft.fft(u[a], axis=axis - 1), axis=axis - 1))
+        for p in (2, 3, 4):
+            m[a, p - 2] = float(np.mean(d ** p))
+    S = m[:, 1].sum() / np.sum(m[:, 0] ** 1.5)
+    F = m[:, 2].sum() / np.sum(m[:, 0] ** 2)
+    return {"E": 0.5 * uu, "uprime": float(uprime), "eps": eps, "lambda": float(lam),
+            "Re_lambda": float(uprime * lam / nu), "eta": float((nu ** 3 / eps) ** 0.25),
+            "S": float(S), "F": float(F), "D": D, "moments": m}
+

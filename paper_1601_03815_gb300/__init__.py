@@ -65,6 +65,7 @@ def _declare(lib):
         "kin_get_velocity": (c_int, [P, P]),
         "kin_step": (c_int, [P, c_int]),
         "kin_stats": (c_int, [P, P, P, P]),
+        "kin_derived_stats": (c_int, [P, P, P]),
         "kin_num_shells": (c_int, [c_int]),
         "kin_sync": (c_int, [P]),
         "kin_step_launches": (c_int, [P]),
@@ -240,6 +241,18 @@ class Sim:
         if spectrum:
             return float(E[0]), float(eps[0]), Ek
         return float(E[0]), float(eps[0])
+
+    DERIVED = ("E", "uprime", "eps", "lambda", "Re_lambda", "eta", "S", "F")
+
+    def derived_stats(self):
+        """kin_derived_stats: dict of E, u', spectral eps, lambda, Re_lambda,
+        eta, S, F and the dissipation spectrum D (per shell)."""
+        out = np.zeros(8)
+        D = np.zeros(num_shells(self.N))
+        _check(lib().kin_derived_stats(self._h, _ptr(out), _ptr(D)), "kin_derived_stats")
+        res = dict(zip(self.DERIVED, (float(v) for v in out)))
+        res["D"] = D
+        return res
 
     def set_tuning(self, block_x: int = 0, tile_y: int = 0, zchunk: int = 0, variant: int = -1):
         _check(lib().kin_set_tuning(self._h, int(block_x), int(tile_y), int(zchunk), int(variant)),

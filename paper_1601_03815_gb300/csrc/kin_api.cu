@@ -71,15 +71,16 @@ size_t state_bytes(const kin_sim* s) { return Q * ncell(s) * storage_bytes(s->st
 
 int ensure_u(kin_sim* s) {
     if (!s->u) CK(cudaMalloc(&s->u, sizeof(double) * 3 * ncell(s)));
-    const size_t need = 2 * (size_t)std::max(stats_blocks(s->N), spectrum_blocks(s->N)) *
-                        (size_t)std::max(kin_num_shells(s->N), 2);
+    const size_t need = std::max(2 * (size_t)std::max(stats_blocks(s->N), spectrum_blocks(s->N)) *
+                                     (size_t)std::max(kin_num_shells(s->N), 2),
+                                 9 * (size_t)deriv_moment_blocks(s->N));
     if (s->red_cap < need) {
         if (s->red) cudaFree(s->red);
         s->red = nullptr;
         CK(cudaMalloc(&s->red, sizeof(double) * need));
         s->red_cap = need;
     }
-    if (!s->red_out) CK(cudaMalloc(&s->red_out, sizeof(double) * (4 + kin_num_shells(s->N))));
+    if (!s->red_out) CK(cudaMalloc(&s->red_out, sizeof(double) * (16 + kin_num_shells(s->N))));
     return KIN_OK;
 }
 
@@ -422,6 +423,70 @@ int kin_stats(kin_sim* s, double* E, double* eps, double* Ek) {
         CK(cudaMemcpyAsync(Ek, s->red_out, sizeof(double) * nsh, cudaMemcpyDeviceToHost, s->stream));
         CK(cudaStreamSynchronize(s->stream));
     }
+    return KIN_OK;
+}
+
+int kin_derived_stats(kin_sim* s, double* out, double* D) {
+    if (int r = valid(s)) return r;
+    if (!out) return fail(KIN_EINVAL, "NULL output");
+    DeviceGuard g(s->device);
+    if (int r = ensure_u(s)) return r;
+    if (int r = ensure_uh(s)) return r;
+    const int N = s->N;
+    const size_t n = ncell(s), nm = nmode(s);
+    CK(velocity_field(s->storage, s->buf[s->cur], shifted(s), N, s->u, s->stream));
+    CK(energy_dissipation(s->u, N, s->nu, s->red, s->red_out, s->stream));
+    double ed[2];
+    CK(cudaMemcpyAsync(ed, s->red_out, sizeof(ed), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (!std::isfinite(ed[0]))
+        return fail(KIN_ENONFINITE, "non-finite statistics at step %lld", (long long)s->step);
+    if (!s->have_d2z) {
+        CKFFT(cufftPlan3d(&s->d2z, N, N, N, CUFFT_D2Z));
+        s->have_d2z = true;
+    }
+    if (!s->have_z2d) {
+        CKFFT(cufftPlan3d(&s->z2d, N, N, N, CUFFT_Z2D));
+        s->have_z2d = true;
+    }
+    CKFFT(cufftSetStream(s->d2z, s->stream));
+    CKFFT(cufftSetStream(s->z2d, s->stream));
+    for (int c = 0; c < 3; ++c)
+        CKFFT(cufftExecD2Z(s->d2z, s->u + c * n, (cufftDoubleComplex*)(s->uh + c * nm)));
+    // shells of |n|^2 |u_hat|^2 / 2 (per mode), scaled below to D(s)
+    const int nsh = kin_num_shells(N);
+    const double inv = 1.0 / ((double)N * N * N);
+    CK(spectrum_shells(s->uh, s->uh + nm, s->uh + 2 * nm, N, nsh, inv, 1, s->red, s->red_out, s->stream));
+    std::vector<double> w(nsh);
+    CK(cudaMemcpyAsync(w.data(), s->red_out, sizeof(double) * nsh, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    // d_a u_a into the velocity scratch, component by component
+    for (int a = 0; a < 3; ++a) {
+        CK(derivative_multiply(s->uh + a * nm, N, a, s->stream));
+        CKFFT(cufftExecZ2D(s->z2d, (cufftDoubleComplex*)(s->uh + a * nm), s->u + a * n));
+    }
+    CK(derivative_moments(s->u, N, s->red, s->red_out, s->stream));
+    double m[9];
+    CK(cudaMemcpyAsync(m, s->red_out, sizeof(m), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->launches += 10;  // velocity, 2 + 2 reductions, 3 multiplies, 2 moment passes
+    const double kf = 2.0 * 3.14159265358979323846 / N, nu = s->nu;
+    double eps = 0.0;
+    for (int k = 0; k < nsh; ++k) {
+        const double d = 2.0 * nu * kf * kf * w[k];
+        if (D) D[k] = d;
+        eps += d;
+    }
+    const double E = ed[0], up = std::sqrt(2.0 * E / 3.0);
+    const double lam = std::sqrt(15.0 * nu / eps) * up;
+    out[0] = E;
+    out[1] = up;
+    out[2] = eps;
+    out[3] = lam;
+    out[4] = up * lam / nu;
+    out[5] = std::pow(nu * nu * nu / eps, 0.25);
+    out[6] = (m[1] + m[4] + m[7]) / (std::pow(m[0], 1.5) + std::pow(m[3], 1.5) + std::pow(m[6], 1.5));
+    out[7] = (m[2] + m[5] + m[8]) / (m[0] * m[0] + m[3] * m[3] + m[6] * m[6]);
     return KIN_OK;
 }
 

@@ -44,6 +44,11 @@ cudaError_t velocity_field32(int storage, const void* state, bool shifted, int N
                              cudaStream_t stream);
 cudaError_t energy_dissipation32(const float* u, int N, double nu, double* partials, double* out,
                                  cudaStream_t stream);
+// Derived statistics: spectral derivative of one component in place, and the
+// moments <d^p> (p = 2, 3, 4) of three derivative fields d[3][N^3] -> out[9].
+cudaError_t derivative_multiply(double2* uh, int N, int axis, cudaStream_t stream);
+cudaError_t derivative_moments(const double* d, int N, double* partial, double* out, cudaStream_t stream);
+int deriv_moment_blocks(int N);
 cudaError_t energy_dissipation(const double* u, int N, double nu, double* partials, double* out,
                                cudaStream_t stream);
 

@@ -362,6 +362,93 @@ __global__ void shell_final_kernel(const double* __restrict__ partial, int nbloc
     out[s] = a;
 }
 
+// ---------------------------------------------------------------------------
+// Spectral derivative d_a u_a of one component: u_hat (half-complex, unscaled
+// D2Z output) times i k_a / N^3, the Nyquist wavenumber of axis a set to zero;
+// the Z2D of the result is the derivative field.
+__global__ void deriv_mult_kernel(double2* __restrict__ uh, int N, int axis) {
+    const int nh = N / 2 + 1;
+    const int kx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kx >= nh) return;
+    const int ky = blockIdx.y, kz = blockIdx.z;
+    const size_t m = (size_t)kx + (size_t)nh * (ky + (size_t)N * kz);
+    int n = axis == 0 ? kx : axis == 1 ? ky : kz;
+    if (axis != 0 && n > N / 2) n -= N;
+    const bool nyquist = (N % 2 == 0) && (n == N / 2 || n == -N / 2);
+    const double inv = 1.0 / ((double)N * N * N);
+    const double k = nyquist ? 0.0 : 2.0 * 3.14159265358979323846 * n / N * inv;
+    const double2 v = uh[m];
+    uh[m] = make_double2(-k * v.y, k * v.x);
+}
+
+constexpr int MOM_THREADS = 256;
+
+// Block partials of sum d^2, d^3, d^4 for the three derivative fields d_a
+// (fixed grid-stride order, then warp and block order): partial[9 b + 3 a + p].
+__global__ void __launch_bounds__(MOM_THREADS)
+    deriv_moments_kernel(const double* __restrict__ d, int N, double* __restrict__ partial) {
+    const size_t n = (size_t)N * N * N;
+    double acc[9];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) acc[j] = 0.0;
+    for (size_t c = (size_t)blockIdx.x * MOM_THREADS + threadIdx.x; c < n; c += (size_t)gridDim.x * MOM_THREADS) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double v = d[a * n + c], v2 = v * v;
+            acc[3 * a] += v2;
+            acc[3 * a + 1] += v2 * v;
+            acc[3 * a + 2] += v2 * v2;
+        }
+    }
+    __shared__ double sh[9][MOM_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        const double w = warp_sum(acc[j]);
+        if (lane == 0) sh[j][wid] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {
+        double t = 0.0;
+        for (int w = 0; w < MOM_THREADS / 32; ++w) t += sh[threadIdx.x][w];
+        partial[9 * (size_t)blockIdx.x + threadIdx.x] = t;
+    }
+}
+
+__global__ void deriv_moments_final_kernel(const double* __restrict__ partial, int nblocks, size_t n,
+                                           double* __restrict__ out) {
+    const int j = threadIdx.x;
+    if (j >= 9) return;
+    double t = 0.0;
+    for (int b = 0; b < nblocks; ++b) t += partial[9 * (size_t)b + j];
+    out[j] = t / (double)n;
+}
+
+int deriv_moment_blocks(int N) {
+    long long n = (long long)N * N * N;
+    long long b = (n + MOM_THREADS * 16 - 1) / (MOM_THREADS * 16);
+    if (b > 608) b = 608;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+cudaError_t derivative_multiply(double2* uh, int N, int axis, cudaStream_t stream) {
+    const int nh = N / 2 + 1;
+    const int bx = nh < 128 ? ((nh + 31) / 32) * 32 : 128;
+    dim3 g((nh + bx - 1) / bx, N, N);
+    deriv_mult_kernel<<<g, bx, 0, stream>>>(uh, N, axis);
+    return cudaGetLastError();
+}
+
+cudaError_t derivative_moments(const double* d, int N, double* partial, double* out, cudaStream_t stream) {
+    const int nb = deriv_moment_blocks(N);
+    deriv_moments_kernel<<<nb, MOM_THREADS, 0, stream>>>(d, N, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    deriv_moments_final_kernel<<<1, 32, 0, stream>>>(partial, nb, (size_t)N * N * N, out);
+    return cudaGetLastError();
+}
+
 cudaError_t spectrum_shells(const void* uh0, const void* uh1, const void* uh2, int N, int nshell,
                             double inv, int weight_n2, double* partial, double* out,
                             cudaStream_t stream) {
