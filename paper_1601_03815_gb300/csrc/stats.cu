@@ -172,6 +172,8 @@ __global__ void __launch_bounds__(RED_THREADS)
 __global__ void __launch_bounds__(RED_THREADS)
     ed32_partial_kernel(const float* __restrict__ u, int N, double* __restrict__ partial) {
     const size_t n = (size_t)N * N * N;
+    // component bases; offsets inside a component fit in 32 bits (N <= 1024)
+    const float* __restrict__ U[3] = {u, u + n, u + 2 * n};
     double se = 0.0, ss = 0.0;
     float fe = 0.0f, fs = 0.0f;
     int rows_in_chunk = 0;
@@ -184,12 +186,10 @@ __global__ void __launch_bounds__(RED_THREADS)
         }
         ++rows_in_chunk;
         const int y = r % N, z = r / N;
-        const size_t row = (size_t)N * r;
-        const size_t rows[3][2] = {{row, row},
-                                   {(size_t)N * (wrap_inc(y, N) + (size_t)N * z),
-                                    (size_t)N * (wrap_dec(y, N) + (size_t)N * z)},
-                                   {(size_t)N * (y + (size_t)N * wrap_inc(z, N)),
-                                    (size_t)N * (y + (size_t)N * wrap_dec(z, N))}};
+        const int row = N * r;
+        const int rows[3][2] = {{row, row},
+                                {N * (wrap_inc(y, N) + N * z), N * (wrap_dec(y, N) + N * z)},
+                                {N * (y + N * wrap_inc(z, N)), N * (y + N * wrap_dec(z, N))}};
         for (int x = threadIdx.x; x < N; x += RED_THREADS) {
             const int xs[3][2] = {{wrap_inc(x, N), wrap_dec(x, N)}, {x, x}, {x, x}};
             float g[3][3];  // g[a][b] = d u_b / d x_a, central differences
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(RED_THREADS)
             for (int a = 0; a < 3; ++a)
 #pragma unroll
                 for (int b = 0; b < 3; ++b)
-                    g[a][b] = 0.5f * (u[b * n + rows[a][0] + xs[a][0]] - u[b * n + rows[a][1] + xs[a][1]]);
+                    g[a][b] = 0.5f * (__ldg(U[b] + rows[a][0] + xs[a][0]) - __ldg(U[b] + rows[a][1] + xs[a][1]));
             float s2 = 0.0f;
 #pragma unroll
             for (int a = 0; a < 3; ++a)
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(RED_THREADS)
                     const float sab = 0.5f * (g[a][b] + g[b][a]);
                     s2 += sab * sab;
                 }
-            const float u0 = u[row + x], u1 = u[n + row + x], u2 = u[2 * n + row + x];
+            const float u0 = __ldg(U[0] + row + x), u1 = __ldg(U[1] + row + x), u2 = __ldg(U[2] + row + x);
             fe += u0 * u0 + u1 * u1 + u2 * u2;
             fs += s2;
         }
