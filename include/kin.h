@@ -115,9 +115,9 @@ int kin_step(kin_sim* sim, int n);
  *          floor(|n| + 1/2) = s of |u_hat|^2 / 2, u_hat = N^-3 FFT(u) (Eq. 27)
  * Any output pointer may be NULL.  Reductions run in a fixed order: the
  * result is bitwise reproducible for a given state.  FP64 storage is reduced
- * in FP64 throughout; for FP32, FP16 and BF16 storage E and eps form each
- * cell's |u|^2 and s_ab s_ab in FP32 and sum them in FP64 (relative error
- * ~1e-7), and Ek is computed from an FP64 velocity field.
+ * in FP64 throughout; for FP32, FP16 and BF16 storage the velocity, E, eps
+ * and the transforms of Ek are formed in FP32 and every sum is taken in FP64
+ * (relative error ~1e-6 and below).
  * Returns KIN_ENONFINITE if E is not finite. */
 int kin_stats(kin_sim* sim, double* E, double* eps, double* Ek);
 

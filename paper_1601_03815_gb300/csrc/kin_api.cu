@@ -222,6 +222,7 @@ void kin_destroy(kin_sim* s) {
     if (s->red_out) cudaFree(s->red_out);
     if (s->have_d2z) cufftDestroy(s->d2z);
     if (s->have_z2d) cufftDestroy(s->z2d);
+    if (s->have_r2c) cufftDestroy(s->r2c);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
 }
@@ -403,22 +404,35 @@ int kin_stats(kin_sim* s, double* E, double* eps, double* Ek) {
         return fail(KIN_ENONFINITE, "non-finite statistics at step %lld", (long long)s->step);
     if (Ek) {
         if (int r = ensure_uh(s)) return r;
-        if (s->storage != ST_F64) {
-            CK(velocity_field(s->storage, s->buf[s->cur], shifted(s), s->N, s->u, s->stream));
-            s->launches += 1;
-        }
         const int N = s->N;
-        if (!s->have_d2z) {
-            CKFFT(cufftPlan3d(&s->d2z, N, N, N, CUFFT_D2Z));
-            s->have_d2z = true;
-        }
-        CKFFT(cufftSetStream(s->d2z, s->stream));
         const size_t nm = nmode(s);
-        for (int c = 0; c < 3; ++c)
-            CKFFT(cufftExecD2Z(s->d2z, s->u + c * ncell(s), (cufftDoubleComplex*)(s->uh + c * nm)));
         const int nsh = kin_num_shells(N);
         const double inv = 1.0 / ((double)N * N * N);
-        CK(spectrum_shells(s->uh, s->uh + nm, s->uh + 2 * nm, N, nsh, inv, 0, s->red, s->red_out, s->stream));
+        if (s->storage == ST_F64) {
+            if (!s->have_d2z) {
+                CKFFT(cufftPlan3d(&s->d2z, N, N, N, CUFFT_D2Z));
+                s->have_d2z = true;
+            }
+            CKFFT(cufftSetStream(s->d2z, s->stream));
+            for (int c = 0; c < 3; ++c)
+                CKFFT(cufftExecD2Z(s->d2z, s->u + c * ncell(s), (cufftDoubleComplex*)(s->uh + c * nm)));
+            CK(spectrum_shells(s->uh, s->uh + nm, s->uh + 2 * nm, N, nsh, inv, 0, s->red, s->red_out,
+                               s->stream));
+        } else {
+            // FP32 transforms of the FP32 velocity already formed above: their
+            // rounding error spreads over every mode, far below the storage's
+            // own rounding in any shell; |u_hat|^2 is summed in FP64.  The
+            // complex output reuses the FP64 spectrum buffer.
+            if (!s->have_r2c) {
+                CKFFT(cufftPlan3d(&s->r2c, N, N, N, CUFFT_R2C));
+                s->have_r2c = true;
+            }
+            CKFFT(cufftSetStream(s->r2c, s->stream));
+            cufftComplex* uh32 = (cufftComplex*)s->uh;
+            for (int c = 0; c < 3; ++c)
+                CKFFT(cufftExecR2C(s->r2c, s->u32 + c * ncell(s), uh32 + c * nm));
+            CK(spectrum_shells32(uh32, uh32 + nm, uh32 + 2 * nm, N, nsh, inv, s->red, s->red_out, s->stream));
+        }
         s->launches += 2;
         CK(cudaMemcpyAsync(Ek, s->red_out, sizeof(double) * nsh, cudaMemcpyDeviceToHost, s->stream));
         CK(cudaStreamSynchronize(s->stream));

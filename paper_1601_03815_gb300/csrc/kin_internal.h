@@ -56,6 +56,9 @@ cudaError_t energy_dissipation(const double* u, int N, double nu, double* partia
 // components (inv = N^-3 for raw D2Z output); with weight_n2 each mode is
 // weighted by |n|^2.  partial[nblocks][nshell], out[nshell].
 int spectrum_blocks(int N);
+// E(k) shells from FP32 transforms (float2 half-complex, unscaled R2C output).
+cudaError_t spectrum_shells32(const void* uh0, const void* uh1, const void* uh2, int N, int nshell,
+                              double inv, double* partial, double* out, cudaStream_t stream);
 cudaError_t spectrum_shells(const void* uh0, const void* uh1, const void* uh2, int N, int nshell,
                             double inv, int weight_n2, double* partial, double* out,
                             cudaStream_t stream);

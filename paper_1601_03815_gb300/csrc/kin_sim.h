@@ -23,8 +23,8 @@ struct kin_sim {
     double* red = nullptr;    // block partials
     double* red_out = nullptr;
     size_t red_cap = 0;
-    cufftHandle d2z = 0, z2d = 0;
-    bool have_d2z = false, have_z2d = false;
+    cufftHandle d2z = 0, z2d = 0, r2c = 0;
+    bool have_d2z = false, have_z2d = false, have_r2c = false;
     int block_lbe = 0, block_dugks = 0;
     int tile_y = 8, zchunk = 0, variant = 0;  // zchunk 0: chosen per launch
     int64_t launches = 0;  // own kernel launches

@@ -300,9 +300,12 @@ int spectrum_blocks(int N) {
     return (int)b;
 }
 
+// CT: double2 (FP64 transform) or float2 (FP32 transform, |u_hat|^2 formed
+// in FP32 and summed in FP64).
+template <typename CT>
 __global__ void __launch_bounds__(SPEC_THREADS)
-    shell_partial_kernel(const double2* __restrict__ u0, const double2* __restrict__ u1,
-                         const double2* __restrict__ u2, int N, int nshell, double inv,
+    shell_partial_kernel(const CT* __restrict__ u0, const CT* __restrict__ u1,
+                         const CT* __restrict__ u2, int N, int nshell, double inv,
                          int weight_n2, double* __restrict__ partial) {
     extern __shared__ double bins[];  // [SPEC_THREADS/32][nshell]
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -327,8 +330,8 @@ __global__ void __launch_bounds__(SPEC_THREADS)
             const int n2 = kx * kx + sy * sy + sz * sz;  // < 2^24: exact in FP32
             // nearest integer to |n|; |n| is never within FP32 rounding of a half-integer
             shell = (int)floorf(sqrtf((float)n2) + 0.5f);
-            const double2 a = u0[m], b = u1[m], c = u2[m];
-            const double amp = (a.x * a.x + a.y * a.y) + (b.x * b.x + b.y * b.y) + (c.x * c.x + c.y * c.y);
+            const CT a = u0[m], b = u1[m], c = u2[m];
+            const double amp = (double)((a.x * a.x + a.y * a.y) + (b.x * b.x + b.y * b.y) + (c.x * c.x + c.y * c.y));
             const double w = (kx > 0 && 2 * kx < N) ? 2.0 : 1.0;
             e = 0.5 * amp * inv * inv * w;
             if (weight_n2) e *= (double)n2;
@@ -449,23 +452,34 @@ cudaError_t derivative_moments(const double* d, int N, double* partial, double* 
     return cudaGetLastError();
 }
 
-cudaError_t spectrum_shells(const void* uh0, const void* uh1, const void* uh2, int N, int nshell,
-                            double inv, int weight_n2, double* partial, double* out,
-                            cudaStream_t stream) {
+template <typename CT>
+static cudaError_t spectrum_shells_t(const void* uh0, const void* uh1, const void* uh2, int N, int nshell,
+                                     double inv, int weight_n2, double* partial, double* out,
+                                     cudaStream_t stream) {
     const int nb = spectrum_blocks(N);
     const size_t smem = sizeof(double) * nshell * (SPEC_THREADS / 32);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(shell_partial_kernel,
+        cudaError_t e = cudaFuncSetAttribute(shell_partial_kernel<CT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    shell_partial_kernel<<<nb, SPEC_THREADS, smem, stream>>>(
-        (const double2*)uh0, (const double2*)uh1, (const double2*)uh2, N, nshell, inv, weight_n2,
-        partial);
+    shell_partial_kernel<CT><<<nb, SPEC_THREADS, smem, stream>>>(
+        (const CT*)uh0, (const CT*)uh1, (const CT*)uh2, N, nshell, inv, weight_n2, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     shell_final_kernel<<<(nshell + 127) / 128, 128, 0, stream>>>(partial, nb, nshell, out);
     return cudaGetLastError();
+}
+
+cudaError_t spectrum_shells(const void* uh0, const void* uh1, const void* uh2, int N, int nshell,
+                            double inv, int weight_n2, double* partial, double* out,
+                            cudaStream_t stream) {
+    return spectrum_shells_t<double2>(uh0, uh1, uh2, N, nshell, inv, weight_n2, partial, out, stream);
+}
+
+cudaError_t spectrum_shells32(const void* uh0, const void* uh1, const void* uh2, int N, int nshell,
+                              double inv, double* partial, double* out, cudaStream_t stream) {
+    return spectrum_shells_t<float2>(uh0, uh1, uh2, N, nshell, inv, 0, partial, out, stream);
 }
 
 // ---------------------------------------------------------------------------

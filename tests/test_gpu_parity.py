@@ -160,7 +160,12 @@ def test_stats_match_oracle(kin, orc, storage):
     # 6e-8 each) and sum them in FP64
     tol = 1e-12 if storage == 3 else 2e-6
     assert abs(E / Eo - 1) < tol and abs(eps / eo - 1) < tol, (E / Eo - 1, eps / eo - 1)
-    np.testing.assert_allclose(Ek, Eko, rtol=1e-10, atol=1e-14 * Eko.max())
+    # E(k): FP64 transforms for FP64 storage, FP32 transforms (FP64 shell sums)
+    # otherwise
+    if storage == 3:
+        np.testing.assert_allclose(Ek, Eko, rtol=1e-10, atol=1e-14 * Eko.max())
+    else:
+        np.testing.assert_allclose(Ek, Eko, rtol=1e-5, atol=1e-8 * Eko.max())
     # fixed-order reductions: bitwise reproducible
     E2, eps2, Ek2 = sim.stats(spectrum=True)
     assert E2 == E and eps2 == eps and np.array_equal(Ek2, Ek)
