@@ -1,4 +1,6 @@
 // Standalone launch of the fused DUGKS step (tile code in dugks_tile.cuh).
+#include <atomic>
+
 #include "dugks_tile.cuh"
 #include "kin_internal.h"
 
@@ -16,12 +18,17 @@ template <typename S, int TY>
 static cudaError_t launch_fused_t(const void* src, void* dst, int N, int zchunk,
                                   const DugksCoef<typename Traits<S>::C>& k, cudaStream_t stream) {
     const size_t smem = fused_smem_bytes<S, TY>();
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(dugks_fused_kernel<S, TY>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the shared-memory limit is a per-device attribute of the kernel: set it
+    // once for every device this process launches on
+    static std::atomic<unsigned long long> configured{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (!bit || !(configured.load() & bit)) {
+        e = cudaFuncSetAttribute(dugks_fused_kernel<S, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured.fetch_or(bit);
     }
     if (zchunk <= 0) zchunk = 32;
     if (zchunk > N) zchunk = N;
