@@ -24,12 +24,13 @@ K0 = math.sqrt(2.0 / 0.14)
 U_PRIME = 0.032
 
 
-def history(N: int, re_lambda: float, T: int, every: int = 20, derived_every: int = 500, seed: int = 1700):
+def history(N: int, re_lambda: float, T: int, every: int = 20, derived_every: int = 500, seed: int = 1700,
+            k0: float = K0):
     out = {}
     for name, scheme, dt in (("lbe", LBE_MRT, 1.0), ("dugks", DUGKS, 0.5)):
         per = int(round(1.0 / dt))  # steps per lattice time unit
         sim = Sim(N, scheme, 0.01, U_PRIME / RS, dt, F32)
-        sim.init_field(seed, K0, re_lambda)
+        sim.init_field(seed, k0, re_lambda)
         rec = {"t": [], "E": [], "eps": [], "derived": []}
         t = 0
         while True:
@@ -51,7 +52,7 @@ def history(N: int, re_lambda: float, T: int, every: int = 20, derived_every: in
         out[name] = rec
     dE = max(abs(a / b - 1) for a, b in zip(out["lbe"]["E"], out["dugks"]["E"]))
     de = max(abs(a / b - 1) for a, b in zip(out["lbe"]["eps"], out["dugks"]["eps"]))
-    return {"N": N, "Re_lambda": re_lambda, "time": T, "u_prime": U_PRIME, "k0": K0, "seed": seed,
+    return {"N": N, "Re_lambda": re_lambda, "time": T, "u_prime": U_PRIME, "k0": k0, "seed": seed,
             "max_rel_diff_E": dE, "max_rel_diff_eps": de, "schemes": out}
 
 
