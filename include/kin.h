@@ -168,10 +168,15 @@ int kin_num_shells(int N);
  *   tile_y   DUGKS fused kernel: rows per tile, 4 or 8
  *   zchunk   DUGKS fused kernel: planes each thread block marches through
  *            (default: as many as keep about two thread blocks per SM)
- *   variant  DUGKS: 0 = fused single launch (default), 1 = two launches
- *            (pre-step into scratch, then flux + update)
+ *   variant  DUGKS: 0 = fused single launch, f-tilde staged by per-thread
+ *            cp.async copies (default); 1 = two launches (pre-step into
+ *            scratch, then flux + update); 2 = fused, f-tilde staged by one
+ *            tensor-memory-accelerator copy per plane (FP32 storage with
+ *            N % 4 == 0, otherwise as 0; bitwise equal to 0)
  * Results do not depend on the launch shape or variant beyond rounding
- * order (the fused and two-launch forms sum the same terms differently). */
+ * order (the fused and two-launch forms sum the same terms differently).
+ * A staging wait of variant 2 that gives up (bounded) makes the next
+ * kin_sync or kin_stats return KIN_ETIMEOUT. */
 int kin_set_tuning(kin_sim* sim, int block_x, int tile_y, int zchunk, int variant);
 
 /* Number of kernel launches one kin_step(sim, 1) enqueues. */

@@ -29,6 +29,8 @@
 // both members.
 #pragma once
 
+#include <cuda.h>
+
 #include <type_traits>
 
 #include "dugks_face.cuh"
@@ -135,6 +137,69 @@ __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Raw staging by the tensor-memory accelerator (FP32, N a multiple of 4): one
+// cp.async.bulk.tensor per plane copies the box x = xs .. xs + 35 (xs = x0 - 1
+// rounded down to a multiple of 4, so the copy starts on a 16-byte boundary),
+// rows y0 - 1 .. y0 + TY, all 19 populations into a slot laid out
+// [population][row][36]; thread `lane` reads element lane + (x0 - 1 - xs).
+// Cells outside the box's periodic image (a tile at the domain edge) arrive
+// as zeros and are patched by their own thread with plain loads.  Each slot
+// has an mbarrier that completes once per copy.
+constexpr int TMA_W = 36;
+template <int TY>
+constexpr int tma_slot_floats() {
+    return ((Q * (TY + 2) * TMA_W + 31) / 32) * 32;  // 128-byte multiple
+}
+template <int TY>
+struct TmaStage {
+    float raw[4][tma_slot_floats<TY>()];
+    unsigned long long bar[4];
+};
+template <int TY>
+constexpr unsigned tma_box_bytes() {
+    return (unsigned)(Q * (TY + 2) * TMA_W * sizeof(float));
+}
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];\n" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+
+// Iterations of a bounded mbarrier wait before the kernel gives up, records
+// the failure and carries on with whatever the slot holds; after one failure a
+// thread no longer waits, so a lost copy costs one limit, not one per plane.
+constexpr long long TMA_WAIT_LIMIT = 1ll << 20;
+
+template <typename S, int TY, bool TMA = false>
+constexpr size_t fused_smem_bytes_v() {
+    using C = typename Traits<S>::C;
+    if constexpr (TMA) return sizeof(FusedSmem<C, TY>) + sizeof(TmaStage<TY>);
+    else return sizeof(FusedSmem<C, TY>) + (kAsyncStage<S> ? sizeof(RawStage<TY>) : kStage16<S> ? sizeof(RawStage16<S, TY>) : 0);
+}
 
 template <typename S, int TY>
 constexpr size_t fused_smem_bytes() {
@@ -304,16 +369,22 @@ __device__ __forceinline__ int wrapc(int v, int n) {
 
 // ------------------------------------------------------------------ the tile
 // One tile (tile coordinates bx, by, bz) of the fused step, run by a
-// 32 x (TY + 2) thread block with fused_smem_bytes<S, TY>() of dynamic shared
-// memory at smem_raw.  Also called by the persistent ensemble kernel.
-template <typename S, int TY>
+// 32 x (TY + 2) thread block with fused_smem_bytes_v<S, TY, TMA>() of dynamic
+// shared memory at smem_raw (128-byte aligned for TMA).  Also called by the
+// persistent ensemble kernel (without TMA).  With TMA (FP32, N % 4 == 0),
+// tmap describes src as a 4-D tensor (x, y, z, population) with a box of
+// TMA_W x (TY + 2) x 1 x 19, and a wait that exceeds TMA_WAIT_LIMIT sets *err.
+template <typename S, int TY, bool TMA = false>
 __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restrict__ dst, int N,
                                            int bx, int by, int bz, int zchunk,
                                            const DugksCoef<typename Traits<S>::C>& kc,
-                                           unsigned char* smem_raw) {
+                                           unsigned char* smem_raw, const CUtensorMap* tmap = nullptr,
+                                           int* err = nullptr) {
     using C = typename Traits<S>::C;
     using P2 = Pr<C>;
+    static_assert(!TMA || std::is_same<S, float>::value, "TMA staging is for FP32 storage");
     FusedSmem<C, TY>& sm = *reinterpret_cast<FusedSmem<C, TY>*>(smem_raw);
+    TmaStage<TY>* tst = reinterpret_cast<TmaStage<TY>*>(smem_raw + sizeof(FusedSmem<C, TY>));
     RawStage<TY>* stage = reinterpret_cast<RawStage<TY>*>(smem_raw + sizeof(FusedSmem<C, TY>));
     RawStage16<S, TY>* stage16 = reinterpret_cast<RawStage16<S, TY>*>(smem_raw + sizeof(FusedSmem<C, TY>));
 
@@ -336,12 +407,32 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
     auto zwrap = [&](int z) { return z < 0 ? z + N : (z >= N ? z - N : z); };
     auto rslot_of = [&](int z) { return (z - z0 + 4) & 3; };
 
+    // TMA staging geometry: box start xs (a multiple of 4), this lane's offset
+    // in the box row, and whether this thread's cell lies outside the box's
+    // unwrapped image (patched with plain loads after every copy)
+    const int xs = x0 - 1 - (((x0 - 1) % 4) + 4) % 4;
+    const int tma_off = x0 - 1 - xs;
+    const bool tma_patch = gxr < 0 || gxr >= N || gyr < 0 || gyr >= N;
+    bool tma_timed_out = false;
+    auto tslot = [&](int z) { return (z - z0 + 1) & 3; };
+    auto tparity = [&](int z) { return (unsigned)(((z - z0 + 1) >> 2) & 1); };
+    auto traw = [&](int s, int i) -> float& { return tst->raw[s][(i * (TY + 2) + row) * TMA_W + lane + tma_off]; };
+
     // 2-byte staging: this lane's word starts at element x0 - 2 + 2 lane (even,
     // so it never straddles the wrap when N is even)
     const bool use16 = kStage16<S> && (N % 2 == 0);
     const size_t rowidx = (size_t)N * gy + (size_t)wrapc(x0 - 2 + 2 * lane, N);
 
     auto issue_plane = [&](int z) {
+        if constexpr (TMA) {
+            if (z <= zend && threadIdx.x == 0 && threadIdx.y == 0) {
+                const int s = tslot(z);
+                fence_proxy_async();  // earlier generic accesses to the slot precede the copy
+                mbar_arrive_expect_tx(&tst->bar[s], tma_box_bytes<TY>());
+                tma_load_4d(&tst->raw[s][0], tmap, xs, y0 - 1, zwrap(z), 0, &tst->bar[s]);
+            }
+            return;
+        }
         if constexpr (kStage16<S>) {
             if (use16) {
                 if (lane <= 16) {
@@ -366,7 +457,10 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
         }
     };
     auto raw_pair = [&](int z, int q) -> P2 {
-        if constexpr (kAsyncStage<S>) {
+        if constexpr (TMA) {
+            const int s = tslot(z);
+            return pmk(traw(s, 2 * q + 1), traw(s, 2 * q + 2));
+        } else if constexpr (kAsyncStage<S>) {
             return stage->raw[rslot_of(z)][q][row][lane];
         } else {
             if constexpr (kStage16<S>) {
@@ -381,7 +475,9 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
         }
     };
     auto raw_rest = [&](int z) -> C {
-        if constexpr (kAsyncStage<S>) {
+        if constexpr (TMA) {
+            return traw(tslot(z), 0);
+        } else if constexpr (kAsyncStage<S>) {
             return stage->raw0[rslot_of(z)][row][lane];
         } else {
             if constexpr (kStage16<S>) {
@@ -457,10 +553,42 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
         cp_async_wait_all();
         if constexpr (kStage16<S>) __syncwarp();
     };
+    // TMA: wait (bounded) for the copy of plane z, then patch this thread's
+    // cell if the box held it only as a zero-filled out-of-range element
+    auto wait_plane = [&](int z) {
+        if constexpr (TMA) {
+            const int s = tslot(z);
+            long long n = 0;
+            while (!tma_timed_out && !mbar_try_wait(&tst->bar[s], tparity(z))) {
+                if (++n > TMA_WAIT_LIMIT) {
+                    tma_timed_out = true;
+                    if (err) atomicExch(err, 1);
+                }
+            }
+            if (tma_patch) {
+                const S* p = src + (size_t)zwrap(z) * nn + colidx;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) traw(s, i) = Traits<S>::load(p + i * plane);
+            }
+        }
+    };
 
+    if constexpr (TMA) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) mbar_init(&tst->bar[k], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+    }
     issue_plane(z0 - 1);
     issue_plane(z0);
-    wait_copies();
+    if constexpr (TMA) {
+        wait_plane(z0 - 1);
+        wait_plane(z0);
+    } else {
+        wait_copies();
+    }
     prestep(z0 - 1, s_m1);
     prestep(z0, s_0);
     issue_plane(z0 + 1);
@@ -484,7 +612,8 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
     for (int z = z0; z <= zend; ++z) {
         const bool last = z == zend;
         if (!last) {
-            if constexpr (kAsyncStage<S> || kStage16<S>) wait_copies();
+            if constexpr (TMA) wait_plane(z + 1);
+            else if constexpr (kAsyncStage<S> || kStage16<S>) wait_copies();
             prestep(z + 1, s_p1);
             if (z + 2 <= zend) issue_plane(z + 2);
         }
@@ -604,6 +733,19 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
         s_m1 = s_0;
         s_0 = s_p1;
         s_p1 = st;
+    }
+    if constexpr (TMA) {
+        // after a wait that gave up, wait (bounded) once more for the last
+        // copy into each slot before the block's shared memory is released
+        if (tma_timed_out) {
+            for (int k = 0; k < 4; ++k) {
+                const int zl = zend - ((tslot(zend) - k + 4) & 3);
+                long long n = 0;
+                if (zl >= z0 - 1)
+                    while (!mbar_try_wait(&tst->bar[k], tparity(zl)) && ++n <= TMA_WAIT_LIMIT) {
+                    }
+            }
+        }
     }
 }
 

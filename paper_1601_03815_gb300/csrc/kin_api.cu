@@ -109,6 +109,33 @@ int auto_zchunk(const kin_sim* s) {
     return (int)zc;
 }
 
+// Tensor maps for the TMA-staged DUGKS step; the cp.async path is used when
+// they cannot be made (FP16/BF16/FP64 storage, N % 4 != 0, no encoder).
+void refresh_tmaps(kin_sim* s) {
+    s->tma_ok = false;
+    if (s->scheme != KIN_DUGKS || s->storage != ST_F32 || s->N % 4 != 0) return;
+    const int ty = s->tile_y == 4 ? 4 : 8;
+    for (int k = 0; k < 2; ++k)
+        if (dugks_make_tmap(s->tmap[k], s->buf[k], s->N, ty) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+    s->tmap_ty = ty;
+    s->tma_ok = true;
+}
+
+// KIN_ETIMEOUT (and clear the flag) if a kernel of this simulation gave up a
+// bounded wait; call after the stream is synchronised.
+int check_device_error(kin_sim* s) {
+    int flag = 0;
+    CK(cudaMemcpy(&flag, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        CK(cudaMemset(s->d_err, 0, sizeof(int)));
+        return fail(KIN_ETIMEOUT, "a staging wait gave up in a DUGKS step; the state is not valid");
+    }
+    return KIN_OK;
+}
+
 int launch_step(kin_sim* s) {
     const void* src = s->buf[s->cur];
     void* dst = s->buf[s->cur ^ 1];
@@ -117,6 +144,9 @@ int launch_step(kin_sim* s) {
         e = lbe_step(s->storage, src, dst, s->N, s->nu, s->block_lbe, s->stream);
     else if (s->variant == 1)
         e = dugks_step(s->storage, src, dst, s->fbp, s->N, s->nu, s->dt, s->block_dugks, s->stream);
+    else if (s->variant == 2 && s->tma_ok)
+        e = dugks_step_fused_tma(s->tmap[s->cur], src, dst, s->N, s->nu, s->dt, s->tmap_ty,
+                                 s->zchunk > 0 ? s->zchunk : auto_zchunk(s), s->d_err, s->stream);
     else
         e = dugks_step_fused(s->storage, src, dst, s->N, s->nu, s->dt, s->tile_y,
                              s->zchunk > 0 ? s->zchunk : auto_zchunk(s), s->stream);
@@ -202,6 +232,15 @@ int kin_create(int N, int scheme, double nu, double Ma, double dt, int storage, 
         e = cudaMemsetAsync(s->buf[k], 0, sb, s->stream);
         if (e != cudaSuccess) return bail(fail(KIN_ECUDA, "memset: %s", cudaGetErrorString(e)));
     }
+    {
+        cudaError_t e = cudaMalloc(&s->d_err, sizeof(int));
+        if (e != cudaSuccess) return bail(fail(KIN_ENOMEM, "error flag: %s", cudaGetErrorString(e)));
+        e = cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream);
+        if (e != cudaSuccess) return bail(fail(KIN_ECUDA, "memset: %s", cudaGetErrorString(e)));
+        e = cudaMallocHost(&s->h_pin, 4 * sizeof(double));
+        if (e != cudaSuccess) return bail(fail(KIN_ENOMEM, "pinned words: %s", cudaGetErrorString(e)));
+    }
+    refresh_tmaps(s);
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return bail(fail(KIN_ECUDA, "sync: %s", cudaGetErrorString(e)));
     *out = s;
@@ -217,6 +256,8 @@ void kin_destroy(kin_sim* s) {
     if (s->fbp) cudaFree(s->fbp);
     if (s->u) cudaFree(s->u);
     if (s->u32) cudaFree(s->u32);
+    if (s->d_err) cudaFree(s->d_err);
+    if (s->h_pin) cudaFreeHost(s->h_pin);
     if (s->uh) cudaFree(s->uh);
     if (s->red) cudaFree(s->red);
     if (s->red_out) cudaFree(s->red_out);
@@ -395,9 +436,14 @@ int kin_stats(kin_sim* s, double* E, double* eps, double* Ek) {
         CK(energy_dissipation32(s->u32, s->N, s->nu, s->red, s->red_out, s->stream));
     }
     s->launches += 3;
-    double ed[2];
-    CK(cudaMemcpyAsync(ed, s->red_out, sizeof(ed), cudaMemcpyDeviceToHost, s->stream));
+    // E, eps and the step kernels' error flag in one synchronisation
+    CK(cudaMemcpyAsync(s->h_pin, s->red_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(s->h_pin + 2, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
+    const double ed[2] = {s->h_pin[0], s->h_pin[1]};
+    int flag = 0;
+    std::memcpy(&flag, s->h_pin + 2, sizeof(int));
+    if (flag) return check_device_error(s);
     if (E) *E = ed[0];
     if (eps) *eps = ed[1];
     if (!std::isfinite(ed[0]) || !std::isfinite(ed[1]))
@@ -514,14 +560,18 @@ int kin_set_tuning(kin_sim* s, int block_x, int tile_y, int zchunk, int variant)
     if (int r = valid(s)) return r;
     if (block_x > 0 && (block_x % 32 || block_x > 1024)) return fail(KIN_EINVAL, "block_x %d", block_x);
     if (tile_y > 0 && tile_y != 4 && tile_y != 8) return fail(KIN_EINVAL, "tile_y must be 4 or 8");
-    if (variant > 1) return fail(KIN_EINVAL, "variant %d", variant);
+    if (variant > 2) return fail(KIN_EINVAL, "variant %d", variant);
     if (variant == 1 && s->scheme == KIN_DUGKS && !s->fbp) {
         const size_t fb = Q * ncell(s) * dugks_scratch_bytes(s->storage);
         DeviceGuard g(s->device);
         CK(cudaMalloc(&s->fbp, fb));
     }
     if (block_x > 0) s->block_lbe = s->block_dugks = block_x;
-    if (tile_y > 0) s->tile_y = tile_y;
+    if (tile_y > 0 && tile_y != s->tile_y) {
+        s->tile_y = tile_y;
+        DeviceGuard g(s->device);
+        refresh_tmaps(s);
+    }
     if (zchunk > 0) s->zchunk = zchunk;
     if (variant >= 0) s->variant = variant;
     return KIN_OK;
@@ -533,7 +583,7 @@ int kin_sync(kin_sim* s) {
     if (int r = valid(s)) return r;
     DeviceGuard g(s->device);
     CK(cudaStreamSynchronize(s->stream));
-    return KIN_OK;
+    return check_device_error(s);
 }
 
 double kin_get_nu(const kin_sim* s) { return s ? s->nu : 0.0; }
