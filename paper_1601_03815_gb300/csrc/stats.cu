@@ -581,20 +581,22 @@ cudaError_t spectrum_shells32(const void* uh0, const void* uh1, const void* uh2,
 }
 
 // ---------------------------------------------------------------------------
+// f = f_eq(0, u) in the storage's compute type: FP64 for FP64 storage, FP32
+// otherwise (FP64 arithmetic on this GPU runs at a small fraction of the FP32
+// rate, and an FP32-stored state needs no more than FP32 arithmetic).
 template <typename S>
 __global__ void feq_kernel(const double* __restrict__ u, bool shifted, int N, size_t plane,
                            S* __restrict__ st) {
+    using C = typename Traits<S>::C;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= N) return;
     const int y = blockIdx.y, z = blockIdx.z;
     const size_t c = (size_t)x + (size_t)N * (y + (size_t)N * z);
-    const double ux = u[c], uy = u[plane + c], uz = u[2 * plane + c];
-    const double usq15 = 1.5 * (ux * ux + uy * uy + uz * uz);
+    const C ux = (C)u[c], uy = (C)u[plane + c], uz = (C)u[2 * plane + c];
+    const C usq15 = C(1.5) * (ux * ux + uy * uy + uz * uz);
     static_for<0, Q>([&](auto ic) {
         constexpr int I = decltype(ic)::value;
-        const double v = feq_i<I>(0.0, ux, uy, uz, usq15);
-        Traits<S>::store(st + I * plane + stored_index<I>(x, y, z, N, shifted),
-                         (typename Traits<S>::C)v);
+        Traits<S>::store(st + I * plane + stored_index<I>(x, y, z, N, shifted), feq_i<I>(C(0), ux, uy, uz, usq15));
     });
 }
 
