@@ -61,6 +61,7 @@ def _load():
             lib.orc_moments.argtypes = [p, p, p]
             lib.orc_mrt_matrix.argtypes = [p]
             lib.orc_mrt_meq.argtypes = [d, d, d, d, p]
+            lib.orc_mrt_meq_w.argtypes = [d, d, d, d, d, d, d, p]
             lib.orc_mrt_rates.argtypes = [d, p]
             lib.orc_mrt_collide.argtypes = [p, p, p, p]
             lib.orc_lbe_step.argtypes = [i, i, i, p, p, p]
@@ -124,9 +125,15 @@ def mrt_matrix() -> np.ndarray:
     return M.reshape(Q, Q)
 
 
-def mrt_meq(drho: float, j) -> np.ndarray:
+def mrt_meq(drho: float, j, omegas=None) -> np.ndarray:
+    """Sec. II.B equilibrium moments; omegas = (omega_eps, omega_epsj,
+    omega_xx), default the paper's (0, -475/63, 0)."""
     out = np.zeros(Q)
-    _load().orc_mrt_meq(float(drho), float(j[0]), float(j[1]), float(j[2]), _ptr(out))
+    if omegas is None:
+        _load().orc_mrt_meq(float(drho), float(j[0]), float(j[1]), float(j[2]), _ptr(out))
+    else:
+        w = [float(v) for v in omegas]
+        _load().orc_mrt_meq_w(float(drho), float(j[0]), float(j[1]), float(j[2]), w[0], w[1], w[2], _ptr(out))
     return out
 
 

@@ -97,12 +97,12 @@ void orc_mrt_matrix(double M[Q * Q]) {
     }
 }
 
-/* Sec. II.B equilibrium moments.  The moment vector holds 3p_xx and 3pi_xx in
- * slots 9 and 10, so slot 9 is 3 * p_xx_eq; pi_eq = omega_xx p_eq = 0 because
- * omega_xx = 0, and eps_eq = omega_eps drho + omega_epsj j^2 / rho0 with
- * omega_eps = 0, omega_epsj = -475/63 (Sec. IV.A). */
-void orc_mrt_meq(double drho, double jx, double jy, double jz, double meq[Q]) {
-    const double omega_eps = 0.0, omega_xx = 0.0, omega_epsj = -475.0 / 63.0;
+/* Sec. II.B equilibrium moments with the model's free parameters: eps_eq =
+ * omega_eps drho + omega_epsj j^2 / rho0, pi_eq = omega_xx p_eq.  The moment
+ * vector holds 3p_xx and 3pi_xx in slots 9 and 10, so slot 9 is 3 * p_xx_eq
+ * and slot 10 is omega_xx * 3 * p_xx_eq. */
+void orc_mrt_meq_w(double drho, double jx, double jy, double jz, double omega_eps, double omega_epsj,
+                   double omega_xx, double meq[Q]) {
     double jj = jx * jx + jy * jy + jz * jz;
     double pxx = (2.0 * jx * jx - (jy * jy + jz * jz)) / (3.0 * RHO0);
     double pww = (jy * jy - jz * jz) / RHO0;
@@ -125,6 +125,11 @@ void orc_mrt_meq(double drho, double jx, double jy, double jz, double meq[Q]) {
     meq[16] = 0.0;
     meq[17] = 0.0;
     meq[18] = 0.0;
+}
+
+/* The paper's values (Sec. IV.A): omega_eps = omega_xx = 0, omega_epsj = -475/63. */
+void orc_mrt_meq(double drho, double jx, double jy, double jz, double meq[Q]) {
+    orc_mrt_meq_w(drho, jx, jy, jz, 0.0, -475.0 / 63.0, 0.0, meq);
 }
 
 /* S = diag(0, s1, s2, 0, s4, 0, s4, 0, s4, s9, s10, s9, s10, s13, s13, s13,

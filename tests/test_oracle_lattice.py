@@ -103,6 +103,27 @@ def test_meq_consistent_with_projected_equilibrium(orc, trial):
     assert abs(meq[2] - (-475 / 63) * (j @ j)) < 1e-15
 
 
+@pytest.mark.parametrize("trial", range(4))
+def test_free_equilibrium_rows_reduce_to_bgk(orc, trial):
+    """Rows 2, 10, 12 (eps, 3 pi_xx, pi_ww) carry the free parameters.  For
+    the D3Q19 quadrature, the projection of the BGK equilibrium is
+    M_2 f_eq = 3 drho - (11/2) j^2 (weights 1/3, 1/18, 1/36 against the eps
+    polynomial, which takes the values 12, -4, 1 on the rest, axis and
+    diagonal velocities) and M_10 f_eq = -(1/2) M_9 f_eq, M_12 f_eq =
+    -(1/2) M_11 f_eq.  With (omega_eps, omega_epsj, omega_xx) = (3, -11/2,
+    -1/2) every one of the 19 equilibrium moments must therefore equal
+    M f_eq: a wrong row, sign or factor in the parametrised rows fails."""
+    drho = RNG.normal() * 1e-2
+    j = RNG.normal(size=3) * 0.1
+    M = orc.mrt_matrix()
+    proj = M @ orc.feq(drho, j)
+    meq = orc.mrt_meq(drho, j, omegas=(3.0, -5.5, -0.5))
+    np.testing.assert_allclose(meq, proj, rtol=0, atol=2e-15)
+    # the paper's parameters are the same rows with other coefficients
+    paper = orc.mrt_meq(drho, j)
+    np.testing.assert_array_equal(orc.mrt_meq(drho, j, omegas=(0.0, -475.0 / 63.0, 0.0)), paper)
+
+
 def test_mrt_rates_reproduce_viscosity(orc):
     """s9 = dt/(3 nu + dt/2) (Sec. IV.A) inverts Eq. 23's nu = (1/s9 - 1/2)/3;
     conserved moments have zero rate."""
