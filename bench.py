@@ -351,9 +351,8 @@ def run_ours(args):
         lbe_e.set_velocity(hu)
         dug_e.set_velocity(hu)
         lbe_e.step(1)
-        dug_e.step(1)
+        dug_e.step_stats(1)
         lbe_e.stats()
-        dug_e.stats()
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
@@ -361,10 +360,11 @@ def run_ours(args):
         lbe_e.set_velocity(hu)
         dug_e.set_velocity(hu)
         for k in range(k_e2e):
+            # the LBE step runs while the DUGKS step and its statistics are
+            # waited for (kin_step_stats: the step also writes the velocity)
             lbe_e.step(1)
-            dug_e.step(1)
+            dug_e.step_stats(1)
             lbe_e.stats()
-            dug_e.stats()
         torch.cuda.synchronize()
         te = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         lbe_e.close()
@@ -373,8 +373,9 @@ def run_ours(args):
                "h2d_bytes_per_step": int(2 * u0.nbytes / k_e2e), "d2h_bytes_per_step": 2 * 2 * 8,
                "steps": k_e2e,
                "what": "kin_set_velocity from pinned host memory for both schemes, then per step "
-                       "kin_step(1) and kin_stats(E, eps) of each, each simulation on its own "
-                       "stream; host wall clock"}
+                       "kin_step(1) of the LBE run, kin_step_stats(1, E, eps) of the DUGKS run and "
+                       "kin_stats(E, eps) of the LBE run, each simulation on its own stream; host "
+                       "wall clock"}
 
     # stability probe (untimed): first check at which E is non-finite, every 5
     # steps up to STABILITY_STEPS, from the seeded field

@@ -121,6 +121,14 @@ int kin_step(kin_sim* sim, int n);
  * Returns KIN_ENONFINITE if E is not finite. */
 int kin_stats(kin_sim* sim, double* E, double* eps, double* Ek);
 
+/* kin_step(sim, n) followed by kin_stats(sim, E, eps, Ek), with the same
+ * results bit for bit.  For DUGKS with FP32, FP16 or BF16 storage on the
+ * fused step (variant 0) the last step also writes the velocity of the state
+ * it produces (Eq. 8, summed in the order the separate velocity pass uses),
+ * so the statistics skip that pass over the 19 populations.  Synchronises the
+ * stream; errors as kin_step and kin_stats. */
+int kin_step_stats(kin_sim* sim, int n, double* E, double* eps, double* Ek);
+
 /* Derived statistics of the current state (Sec. III; synchronises the stream):
  *   out[0] E          <u.u>/2
  *   out[1] u'         sqrt(<u.u>/3)

@@ -65,6 +65,7 @@ def _declare(lib):
         "kin_get_velocity": (c_int, [P, P]),
         "kin_step": (c_int, [P, c_int]),
         "kin_stats": (c_int, [P, P, P, P]),
+        "kin_step_stats": (c_int, [P, c_int, P, P, P]),
         "kin_derived_stats": (c_int, [P, P, P]),
         "kin_num_shells": (c_int, [c_int]),
         "kin_sync": (c_int, [P]),
@@ -238,6 +239,18 @@ class Sim:
         Ek = np.zeros(num_shells(self.N)) if spectrum else None
         _check(lib().kin_stats(self._h, _ptr(E), _ptr(eps), None if Ek is None else _ptr(Ek)),
                "kin_stats")
+        if spectrum:
+            return float(E[0]), float(eps[0]), Ek
+        return float(E[0]), float(eps[0])
+
+    def step_stats(self, n: int = 1, spectrum: bool = False):
+        """kin_step_stats: n steps, then (E, eps) or (E, eps, Ek) of the new
+        state; equal to step(n) followed by stats()."""
+        E = np.zeros(1)
+        eps = np.zeros(1)
+        Ek = np.zeros(num_shells(self.N)) if spectrum else None
+        _check(lib().kin_step_stats(self._h, int(n), _ptr(E), _ptr(eps), None if Ek is None else _ptr(Ek)),
+               "kin_step_stats")
         if spectrum:
             return float(E[0]), float(eps[0]), Ek
         return float(E[0]), float(eps[0])

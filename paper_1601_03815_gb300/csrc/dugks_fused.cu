@@ -6,17 +6,19 @@
 
 namespace kin {
 
-template <typename S, int TY>
+// VEL: also write the velocity of the new state to uvel (FP32-computed storage).
+template <typename S, int TY, bool VEL>
 __global__ void __launch_bounds__(32 * (TY + 2), 1)
     dugks_fused_kernel(const S* __restrict__ src, S* __restrict__ dst, int N, int zchunk,
-                       DugksCoef<typename Traits<S>::C> kc) {
+                       DugksCoef<typename Traits<S>::C> kc, float* __restrict__ uvel) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    dugks_tile<S, TY>(src, dst, N, blockIdx.x, blockIdx.y, blockIdx.z, zchunk, kc, smem_raw);
+    dugks_tile<S, TY, false, VEL>(src, dst, N, blockIdx.x, blockIdx.y, blockIdx.z, zchunk, kc, smem_raw,
+                                  nullptr, nullptr, uvel);
 }
 
-template <typename S, int TY>
+template <typename S, int TY, bool VEL>
 static cudaError_t launch_fused_t(const void* src, void* dst, int N, int zchunk,
-                                  const DugksCoef<typename Traits<S>::C>& k, cudaStream_t stream) {
+                                  const DugksCoef<typename Traits<S>::C>& k, float* uvel, cudaStream_t stream) {
     const size_t smem = fused_smem_bytes<S, TY>();
     // the shared-memory limit is a per-device attribute of the kernel: set it
     // once for every device this process launches on
@@ -26,7 +28,8 @@ static cudaError_t launch_fused_t(const void* src, void* dst, int N, int zchunk,
     if (e != cudaSuccess) return e;
     const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
     if (!bit || !(configured.load() & bit)) {
-        e = cudaFuncSetAttribute(dugks_fused_kernel<S, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(dugks_fused_kernel<S, TY, VEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
         if (e != cudaSuccess) return e;
         configured.fetch_or(bit);
     }
@@ -34,20 +37,25 @@ static cudaError_t launch_fused_t(const void* src, void* dst, int N, int zchunk,
     if (zchunk > N) zchunk = N;
     dim3 block(32, TY + 2);
     dim3 grid((N + 29) / 30, (N + TY - 1) / TY, (N + zchunk - 1) / zchunk);
-    dugks_fused_kernel<S, TY><<<grid, block, smem, stream>>>((const S*)src, (S*)dst, N, zchunk, k);
+    dugks_fused_kernel<S, TY, VEL><<<grid, block, smem, stream>>>((const S*)src, (S*)dst, N, zchunk, k, uvel);
     return cudaGetLastError();
 }
 
 template <typename S>
 static cudaError_t launch_fused(const void* src, void* dst, int N, double nu, double dt, int ty,
-                                int zchunk, cudaStream_t stream) {
+                                int zchunk, float* uvel, cudaStream_t stream) {
     using C = typename Traits<S>::C;
     const DugksCoef<C> k = dugks_coef<C>(nu, dt);
     if constexpr (sizeof(C) == 8) {
-        return launch_fused_t<S, 4>(src, dst, N, zchunk, k, stream);
+        if (uvel) return cudaErrorInvalidValue;  // FP64 storage keeps the FP64 statistics path
+        return launch_fused_t<S, 4, false>(src, dst, N, zchunk, k, nullptr, stream);
     } else {
-        if (ty == 4) return launch_fused_t<S, 4>(src, dst, N, zchunk, k, stream);
-        return launch_fused_t<S, 8>(src, dst, N, zchunk, k, stream);
+        if (uvel) {
+            if (ty == 4) return launch_fused_t<S, 4, true>(src, dst, N, zchunk, k, uvel, stream);
+            return launch_fused_t<S, 8, true>(src, dst, N, zchunk, k, uvel, stream);
+        }
+        if (ty == 4) return launch_fused_t<S, 4, false>(src, dst, N, zchunk, k, nullptr, stream);
+        return launch_fused_t<S, 8, false>(src, dst, N, zchunk, k, nullptr, stream);
     }
 }
 
@@ -118,12 +126,12 @@ cudaError_t dugks_make_tmap(void* tmap, const void* base, int N, int ty) {
 }
 
 cudaError_t dugks_step_fused(int storage, const void* src, void* dst, int N, double nu, double dt,
-                             int ty, int zchunk, cudaStream_t stream) {
+                             int ty, int zchunk, cudaStream_t stream, float* uvel) {
     switch (storage) {
-        case ST_F32: return launch_fused<float>(src, dst, N, nu, dt, ty, zchunk, stream);
-        case ST_F16: return launch_fused<__half>(src, dst, N, nu, dt, ty, zchunk, stream);
-        case ST_BF16: return launch_fused<__nv_bfloat16>(src, dst, N, nu, dt, ty, zchunk, stream);
-        case ST_F64: return launch_fused<double>(src, dst, N, nu, dt, ty, zchunk, stream);
+        case ST_F32: return launch_fused<float>(src, dst, N, nu, dt, ty, zchunk, uvel, stream);
+        case ST_F16: return launch_fused<__half>(src, dst, N, nu, dt, ty, zchunk, uvel, stream);
+        case ST_BF16: return launch_fused<__nv_bfloat16>(src, dst, N, nu, dt, ty, zchunk, uvel, stream);
+        case ST_F64: return launch_fused<double>(src, dst, N, nu, dt, ty, zchunk, uvel, stream);
     }
     return cudaErrorInvalidValue;
 }

@@ -374,15 +374,18 @@ __device__ __forceinline__ int wrapc(int v, int n) {
 // persistent ensemble kernel (without TMA).  With TMA (FP32, N % 4 == 0),
 // tmap describes src as a 4-D tensor (x, y, z, population) with a box of
 // TMA_W x (TY + 2) x 1 x 19, and a wait that exceeds TMA_WAIT_LIMIT sets *err.
-template <typename S, int TY, bool TMA = false>
+// With VEL (FP32-computed storage) the tile also writes rho0 u = sum xi f of
+// the stored new state (Eq. 8) to uvel[3][N^3], summed in population order.
+template <typename S, int TY, bool TMA = false, bool VEL = false>
 __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restrict__ dst, int N,
                                            int bx, int by, int bz, int zchunk,
                                            const DugksCoef<typename Traits<S>::C>& kc,
                                            unsigned char* smem_raw, const CUtensorMap* tmap = nullptr,
-                                           int* err = nullptr) {
+                                           int* err = nullptr, float* __restrict__ uvel = nullptr) {
     using C = typename Traits<S>::C;
     using P2 = Pr<C>;
     static_assert(!TMA || std::is_same<S, float>::value, "TMA staging is for FP32 storage");
+    static_assert(!VEL || std::is_same<C, float>::value, "the fused velocity serves FP32-computed storage");
     FusedSmem<C, TY>& sm = *reinterpret_cast<FusedSmem<C, TY>*>(smem_raw);
     TmaStage<TY>* tst = reinterpret_cast<TmaStage<TY>*>(smem_raw + sizeof(FusedSmem<C, TY>));
     RawStage<TY>* stage = reinterpret_cast<RawStage<TY>*>(smem_raw + sizeof(FusedSmem<C, TY>));
@@ -701,6 +704,18 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
             });
             if (valid) {
                 const size_t c = (size_t)(z - 1) * nn + colidx;
+                [[maybe_unused]] C uv[3] = {C(0), C(0), C(0)};
+                // velocity sums in population order: the same additions as the
+                // separate velocity pass over the stored state
+                [[maybe_unused]] auto vel_add = [&](auto ic, C v) {
+                    constexpr int I = decltype(ic)::value;
+                    if constexpr (cx(I) > 0) uv[0] += v;
+                    if constexpr (cx(I) < 0) uv[0] -= v;
+                    if constexpr (cy(I) > 0) uv[1] += v;
+                    if constexpr (cy(I) < 0) uv[1] -= v;
+                    if constexpr (cz(I) > 0) uv[2] += v;
+                    if constexpr (cz(I) < 0) uv[2] -= v;
+                };
                 static_for<0, NPAIR>([&](auto pc) {
                     constexpr int PP = decltype(pc)::value;
                     const P2 xb = sm.ring[s_m1][PP][row][lane];
@@ -709,9 +724,18 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
                     const P2 o = pfma(kc.dts, Dprev[PP], t);
                     Traits<S>::store(dst + (2 * PP + 1) * plane + c, o.x);
                     Traits<S>::store(dst + (2 * PP + 2) * plane + c, o.y);
+                    if constexpr (VEL) {
+                        vel_add(std::integral_constant<int, 2 * PP + 1>{}, Traits<S>::rt(o.x));
+                        vel_add(std::integral_constant<int, 2 * PP + 2>{}, Traits<S>::rt(o.y));
+                    }
                 });
                 const C xb0 = sm.ring0[s_m1][row][lane];
                 Traits<S>::store(dst + c, fma(C(1.0 / 3.0), xb0 - raw_rest(z - 1), xb0));
+                if constexpr (VEL) {
+                    uvel[c] = uv[0];
+                    uvel[plane + c] = uv[1];
+                    uvel[2 * plane + c] = uv[2];
+                }
             }
         }
         __syncthreads();  // my of plane z complete; fy of plane z - 1 consumed

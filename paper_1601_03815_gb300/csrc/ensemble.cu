@@ -317,6 +317,7 @@ int run(kin_ensemble* e, int nsteps, int stall_test) {
     for (kin_sim* s : e->members) {
         s->cur ^= (nsteps & 1);
         s->step += nsteps;
+        s->epoch += 1;
     }
     return KIN_OK;
 }

@@ -136,7 +136,15 @@ int check_device_error(kin_sim* s) {
     return KIN_OK;
 }
 
-int launch_step(kin_sim* s) {
+// The step goes to the fused cp.async DUGKS kernel, which can also write the
+// new state's velocity (FP32-computed storage).
+bool fused_velocity_ok(const kin_sim* s) {
+    return s->scheme == KIN_DUGKS && s->storage != ST_F64 && s->variant != 1 && !(s->variant == 2 && s->tma_ok);
+}
+
+// One step; with uvel (only where fused_velocity_ok) the step also leaves the
+// new state's velocity in s->u32.
+int launch_step(kin_sim* s, float* uvel = nullptr) {
     const void* src = s->buf[s->cur];
     void* dst = s->buf[s->cur ^ 1];
     cudaError_t e;
@@ -149,11 +157,13 @@ int launch_step(kin_sim* s) {
                                  s->zchunk > 0 ? s->zchunk : auto_zchunk(s), s->d_err, s->stream);
     else
         e = dugks_step_fused(s->storage, src, dst, s->N, s->nu, s->dt, s->tile_y,
-                             s->zchunk > 0 ? s->zchunk : auto_zchunk(s), s->stream);
+                             s->zchunk > 0 ? s->zchunk : auto_zchunk(s), s->stream, uvel);
     if (e != cudaSuccess) return fail(KIN_ECUDA, "step launch: %s", cudaGetErrorString(e));
     s->launches += kin_step_launches(s);
     s->cur ^= 1;
     s->step += 1;
+    s->epoch += 1;
+    if (uvel) s->u32_epoch = s->epoch;
     return KIN_OK;
 }
 
@@ -277,6 +287,7 @@ int kin_set_velocity(kin_sim* s, const double* u) {
     CK(equilibrium_from_velocity(s->storage, s->u, shifted(s), s->N, s->buf[s->cur], s->stream));
     CK(cudaStreamSynchronize(s->stream));
     s->step = 0;
+    s->epoch += 1;
     return KIN_OK;
 }
 
@@ -340,6 +351,7 @@ int kin_init_field(kin_sim* s, uint64_t seed, double k0, double re_lambda) {
         s->nu = up2 * std::sqrt(15.0 / (2.0 * omega)) / re_lambda;
     }
     s->step = 0;
+    s->epoch += 1;
     return KIN_OK;
 }
 
@@ -355,6 +367,7 @@ int kin_set_f(kin_sim* s, const double* f) {
     }
     CK(cudaStreamSynchronize(s->stream));
     s->step = 0;
+    s->epoch += 1;
     return KIN_OK;
 }
 
@@ -421,6 +434,17 @@ int kin_step(kin_sim* s, int n) {
     return KIN_OK;
 }
 
+int kin_step_stats(kin_sim* s, int n, double* E, double* eps, double* Ek) {
+    if (int r = valid(s)) return r;
+    if (n < 0) return fail(KIN_EINVAL, "negative step count");
+    DeviceGuard g(s->device);
+    const bool fuse = n > 0 && fused_velocity_ok(s);
+    if (fuse && !s->u32) CK(cudaMalloc(&s->u32, sizeof(float) * 3 * ncell(s)));
+    for (int k = 0; k < n; ++k)
+        if (int r = launch_step(s, fuse && k == n - 1 ? s->u32 : nullptr)) return r;
+    return kin_stats(s, E, eps, Ek);
+}
+
 int kin_stats(kin_sim* s, double* E, double* eps, double* Ek) {
     if (int r = valid(s)) return r;
     DeviceGuard g(s->device);
@@ -428,14 +452,21 @@ int kin_stats(kin_sim* s, double* E, double* eps, double* Ek) {
     if (s->storage == ST_F64) {
         CK(velocity_field(s->storage, s->buf[s->cur], shifted(s), s->N, s->u, s->stream));
         CK(energy_dissipation(s->u, s->N, s->nu, s->red, s->red_out, s->stream));
+        s->launches += 3;
     } else {
         // FP32 arithmetic per cell (FP64 on this GPU runs at a small fraction
-        // of the FP32 rate), FP64 sums
+        // of the FP32 rate), FP64 sums; the velocity pass is skipped when u32
+        // already holds this state's velocity (left by the step that made it,
+        // or by an earlier call)
         if (!s->u32) CK(cudaMalloc(&s->u32, sizeof(float) * 3 * ncell(s)));
-        CK(velocity_field32(s->storage, s->buf[s->cur], shifted(s), s->N, s->u32, s->stream));
+        if (s->u32_epoch != s->epoch) {
+            CK(velocity_field32(s->storage, s->buf[s->cur], shifted(s), s->N, s->u32, s->stream));
+            s->launches += 1;
+            s->u32_epoch = s->epoch;
+        }
         CK(energy_dissipation32(s->u32, s->N, s->nu, s->red, s->red_out, s->stream));
+        s->launches += 2;
     }
-    s->launches += 3;
     // E, eps and the step kernels' error flag in one synchronisation
     CK(cudaMemcpyAsync(s->h_pin, s->red_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaMemcpyAsync(s->h_pin + 2, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
@@ -477,6 +508,7 @@ int kin_stats(kin_sim* s, double* E, double* eps, double* Ek) {
             cufftComplex* uh32 = (cufftComplex*)s->uh;
             for (int c = 0; c < 3; ++c)
                 CKFFT(cufftExecR2C(s->r2c, s->u32 + c * ncell(s), uh32 + c * nm));
+            s->u32_epoch = ~0ull;  // the transforms may use their input as work space
             CK(spectrum_shells32(uh32, uh32 + nm, uh32 + 2 * nm, N, nsh, inv, s->red, s->red_out, s->stream));
         }
         s->launches += 2;

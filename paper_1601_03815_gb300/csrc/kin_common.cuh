@@ -59,18 +59,22 @@ struct Traits<float> {
     using C = float;
     static __device__ __forceinline__ C load(const float* p) { return __ldg(p); }
     static __device__ __forceinline__ void store(float* p, C v) { *p = v; }
+    // the value a store followed by a load returns
+    static __device__ __forceinline__ C rt(C v) { return v; }
 };
 template <>
 struct Traits<double> {
     using C = double;
     static __device__ __forceinline__ C load(const double* p) { return __ldg(p); }
     static __device__ __forceinline__ void store(double* p, C v) { *p = v; }
+    static __device__ __forceinline__ C rt(C v) { return v; }
 };
 template <>
 struct Traits<__half> {
     using C = float;
     static __device__ __forceinline__ C load(const __half* p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ void store(__half* p, C v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ C rt(C v) { return __half2float(__float2half_rn(v)); }
 };
 template <>
 struct Traits<__nv_bfloat16> {
@@ -79,6 +83,7 @@ struct Traits<__nv_bfloat16> {
         return __bfloat162float(__ldg(p));
     }
     static __device__ __forceinline__ void store(__nv_bfloat16* p, C v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ C rt(C v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 };
 
 // ---------------------------------------------------------------------------

@@ -32,8 +32,10 @@ cudaError_t dugks_step(int storage, const void* src, void* dst, void* fbp, int N
 cudaError_t dugks_step_fused_tma(const void* tmap, const void* src, void* dst, int N, double nu, double dt,
                                  int tile_y, int zchunk, int* err, cudaStream_t stream);
 cudaError_t dugks_make_tmap(void* tmap, const void* base, int N, int tile_y);
+// uvel: NULL, or (FP32-computed storage) uvel[3][N^3] receives the velocity
+// of the new state, bitwise equal to velocity_field32 of it.
 cudaError_t dugks_step_fused(int storage, const void* src, void* dst, int N, double nu, double dt,
-                             int tile_y, int zchunk, cudaStream_t stream);
+                             int tile_y, int zchunk, cudaStream_t stream, float* uvel = nullptr);
 
 // Compute-type size of the DUGKS scratch element (4 or 8 bytes).
 size_t dugks_scratch_bytes(int storage);

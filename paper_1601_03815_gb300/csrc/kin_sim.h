@@ -35,6 +35,9 @@ struct kin_sim {
     int* d_err = nullptr;  // set by a kernel whose bounded wait gave up
     double* h_pin = nullptr;  // pinned host words: E, eps, and the error flag
     int64_t launches = 0;  // own kernel launches
+    // state version: bumped by every step and every write of the state; u32
+    // holds the velocity of the state of version u32_epoch
+    uint64_t epoch = 0, u32_epoch = ~0ull;
 };
 
 
