@@ -191,13 +191,17 @@ def extras(args) -> dict:
 
     out = {}
     out["ensemble"] = ens_mod.measure(steps=500)
-    reqs = srv_mod.poisson_requests(4.0, args.serving_seconds, seed=2024)
-    backend = srv_mod.GpuBackend()
-    _, rep = srv_mod.Server(backend, 64 * 2 ** 30, 64, 50).run(reqs)
-    backend.close()
-    rep["arrival_window_s"] = args.serving_seconds
-    rep["rate_per_s"] = 4.0
-    out["serving"] = rep
+    # the same seeded arrival trace through both serving backends; the first
+    # (per-simulation streams) is the serving loop's default
+    for key, name in (("serving", "streams"), ("serving_ensemble_backend", "ensemble")):
+        reqs = srv_mod.poisson_requests(4.0, args.serving_seconds, seed=2024)
+        backend = srv_mod.BACKENDS[name]()
+        _, rep = srv_mod.Server(backend, 64 * 2 ** 30, 64, 50).run(reqs)
+        backend.close()
+        rep["backend"] = name
+        rep["arrival_window_s"] = args.serving_seconds
+        rep["rate_per_s"] = 4.0
+        out[key] = rep
     out["precision"] = prec_mod.study(args.N, 1000)
     return out
 

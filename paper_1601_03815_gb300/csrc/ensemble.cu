@@ -110,22 +110,26 @@ __global__ void __launch_bounds__(32 * (TY + 2), 1)
                 const int c0 = item.y * M.lbe_nodes;
                 const int c1 = (int)min((long long)c0 + M.lbe_nodes, (long long)plane);
                 constexpr int K = 3;  // nodes per thread in flight
+                const MrtRates<float> rates = M.rates;
                 int c = c0 + tid;
                 for (; c + (K - 1) * NT < c1; c += K * NT) {
                     int cs[K];
 #pragma unroll
                     for (int k = 0; k < K; ++k) cs[k] = c + k * NT;
-                    lbe_nodes<K, float, true>(src, dst, N, plane, cs, M.rates);
+                    lbe_nodes<K, float, true>(src, dst, N, plane, cs, rates);
                 }
                 for (; c < c1; c += NT) {
                     const int cs[1] = {c};
-                    lbe_nodes<1, float, true>(src, dst, N, plane, cs, M.rates);
+                    lbe_nodes<1, float, true>(src, dst, N, plane, cs, rates);
                 }
             } else {
                 const int per = M.tiles_x * M.tiles_y;
                 const int bz = item.y / per, r = item.y % per;
-                dugks_tile<float, TY>(src, dst, N, r % M.tiles_x, r / M.tiles_x, bz, M.zchunk, M.coef,
-                                      smem_raw);
+                // a local copy of the member's coefficients: passed as a
+                // reference into the member table in global memory, the items
+                // ran 13 % slower
+                const DugksCoef<float> kc = M.coef;
+                dugks_tile<float, TY>(src, dst, N, r % M.tiles_x, r / M.tiles_x, bz, M.zchunk, kc, smem_raw);
             }
             __syncthreads();
             if (tid == 0) red_release_add(&done[item.x], 1u);

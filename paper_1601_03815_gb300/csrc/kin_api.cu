@@ -7,10 +7,13 @@
 
 #include <cufft.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
+#include <queue>
 #include <vector>
 
 using namespace kin;
@@ -99,14 +102,65 @@ int valid(const kin_sim* s) {
 // Planes per fused-DUGKS thread block when the caller has not chosen: as long
 // as possible (fewer halo planes re-read) while the grid still has about two
 // blocks per SM.
-int auto_zchunk(const kin_sim* s) {
-    const int nsm = s->num_sms;
-    const long long tiles_xy = (long long)((s->N + 29) / 30) * ((s->N + s->tile_y - 1) / s->tile_y);
-    long long zc = (long long)s->N * tiles_xy / (2LL * nsm);
-    zc = zc / 8 * 8;
-    if (zc < 8) zc = 8;
-    if (zc > s->N) zc = s->N;
-    return (int)zc;
+// Makespan, in plane-times, of the fused DUGKS launch with z chunks of zc
+// planes: cols blocks per chunk, issued chunk by chunk (the grid's z index
+// varies slowest), each occupying one of nsm SMs for its planes plus the
+// ~1.5 plane-times of its prologue (two pre-steps and one cell view before
+// the first face); every block goes to the SM that frees first.
+double dugks_makespan(int N, long long cols, int zc, int nsm) {
+    constexpr double kPrologue = 1.5;
+    std::priority_queue<double, std::vector<double>, std::greater<double>> sm;
+    for (int k = 0; k < nsm; ++k) sm.push(0.0);
+    double end = 0.0;
+    for (int z0 = 0; z0 < N; z0 += zc) {
+        const double c = std::min(zc, N - z0) + kPrologue;
+        for (long long b = 0; b < cols; ++b) {
+            const double t = sm.top() + c;
+            sm.pop();
+            sm.push(t);
+            end = std::max(end, t);
+        }
+    }
+    return end;
+}
+
+// Planes per block of the fused DUGKS step.  With one block per SM the step
+// lasts as long as its busiest SM, so a chunk length that leaves the last
+// wave nearly empty costs up to a third of the step (128^3: 32 planes give
+// 320 blocks, 2.1 waves).  When the columns alone fill fewer than 1.5 waves,
+// every candidate is scored by the schedule above and the shortest taken (the
+// longest chunk among those within 0.5 %: fewer halo planes re-read, longer
+// runs of neighbouring columns in L2); measured at 32^3-192^3 this is within
+// 1 % of the best chunk of a sweep.  Larger grids keep chunks that make about
+// two waves of blocks, rounded down to 8 planes: at 256^3 that is 240 + 16
+// planes, the measured optimum, which the schedule model (blind to cache
+// effects) misranks by ~1 %.
+int auto_zchunk(kin_sim* s) {
+    const int ty = s->storage == ST_F64 ? 4 : (s->tile_y == 4 ? 4 : 8);
+    if (s->zc_auto > 0 && s->zc_auto_ty == ty) return s->zc_auto;
+    const int N = s->N;
+    const long long cols = (long long)((N + 29) / 30) * ((N + ty - 1) / ty);
+    s->zc_auto_ty = ty;
+    if (2 * cols >= 3LL * s->num_sms) {
+        long long zc = (long long)N * cols / (2LL * s->num_sms);
+        zc = std::max(8LL, std::min<long long>(zc / 8 * 8, N));
+        s->zc_auto = (int)zc;
+        return s->zc_auto;
+    }
+    constexpr long long kMaxBlocks = 20000;
+    int best_zc = N;
+    double best = -1.0;
+    for (int zc = N; zc >= 4; --zc) {
+        const int nz = (N + zc - 1) / zc;
+        if (nz > 64 || cols * nz > kMaxBlocks) continue;
+        const double m = dugks_makespan(N, cols, zc, s->num_sms);
+        if (best < 0.0 || m < best * (1.0 - 0.005)) {
+            best = m;
+            best_zc = zc;
+        }
+    }
+    s->zc_auto = best_zc;
+    return best_zc;
 }
 
 // Tensor maps for the TMA-staged DUGKS step; the cp.async path is used when

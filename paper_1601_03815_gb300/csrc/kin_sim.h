@@ -27,6 +27,7 @@ struct kin_sim {
     bool have_d2z = false, have_z2d = false, have_r2c = false;
     int block_lbe = 0, block_dugks = 0;
     int tile_y = 8, zchunk = 0, variant = 0;  // zchunk 0: chosen per launch
+    int zc_auto = 0, zc_auto_ty = 0;  // the chosen z chunk and the tile height it was chosen for
     // TMA staging of the fused DUGKS step (FP32, N % 4 == 0): tensor maps of
     // buf[0] and buf[1] for the current tile_y (CUtensorMap, 128 bytes each)
     alignas(64) unsigned char tmap[2][128] = {};

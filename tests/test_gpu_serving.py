@@ -1,5 +1,6 @@
-"""Serving on the GPU: continuous batching through the persistent ensemble
-kernel; each request's final state is bitwise the same alone and in the mix."""
+"""Serving on the GPU with both backends (per-simulation streams, persistent
+ensemble kernel): each request's final state is bitwise the same alone and
+in the mix, and later arrivals join running requests."""
 import numpy as np
 import pytest
 
@@ -15,9 +16,11 @@ def _requests():
             Request(rid=3, N=24, scheme=0, re_lambda=40.0, steps=44, seed=14, arrival=0.0, want_f=True)]
 
 
-def test_result_is_the_same_alone_and_in_the_mix(kin):
-    from paper_1601_03815_gb300.serving import GpuBackend, Server
+@pytest.mark.parametrize("backend", ["streams", "ensemble"])
+def test_result_is_the_same_alone_and_in_the_mix(kin, backend):
+    from paper_1601_03815_gb300.serving import BACKENDS, Server
 
+    GpuBackend = BACKENDS[backend]
     reqs = _requests()
     be = GpuBackend()
     mix, rep = Server(be, hbm_budget=2 ** 31, max_active=8, chunk=10).run(reqs)
@@ -32,9 +35,11 @@ def test_result_is_the_same_alone_and_in_the_mix(kin):
         assert alone[0].E == m.E and alone[0].eps == m.eps
 
 
-def test_requests_arriving_later_join_running_ones(kin):
-    from paper_1601_03815_gb300.serving import GpuBackend, Request, Server
+@pytest.mark.parametrize("backend", ["streams", "ensemble"])
+def test_requests_arriving_later_join_running_ones(kin, backend):
+    from paper_1601_03815_gb300.serving import BACKENDS, Request, Server
 
+    GpuBackend = BACKENDS[backend]
     # the first request runs long enough (1000 ticks) that the later arrivals
     # find it still resident however fast a tick is
     reqs = [Request(rid=k, N=16, scheme=k % 2, re_lambda=25.0, steps=20000 if k == 0 else 400,
