@@ -25,7 +25,7 @@ from . import DUGKS, F32, LBE_MRT, Ensemble, Sim
 
 REFERENCE_SIZES = ((32, 8), (64, 8), (96, 6), (128, 2))
 TUNE_TILE_Y = (4, 8)
-TUNE_ZCHUNK = (8, 16, 32)
+TUNE_ZCHUNK = (8, 16, 32, 64, 128)
 TUNE_LBE_NODES = (1024, 4096, 16384)
 
 
