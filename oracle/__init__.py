@@ -66,6 +66,8 @@ def _load():
             lib.orc_mrt_collide.argtypes = [p, p, p, p]
             lib.orc_lbe_step.argtypes = [i, i, i, p, p, p]
             lib.orc_lbe_step.restype = i
+            lib.orc_lbe_consistent_step.argtypes = [i, i, i, p, p, p, p]
+            lib.orc_lbe_consistent_step.restype = i
             lib.orc_dugks_tau.argtypes = [d]
             lib.orc_dugks_tau.restype = d
             lib.orc_dugks_prestep_cell.argtypes = [d, d, p, p, p]
@@ -170,6 +172,39 @@ def lbe_step(f, nu: float | None = None, s=None) -> np.ndarray:
     if rc != 0:
         raise RuntimeError("orc_lbe_step failed: %d" % rc)
     return out
+
+
+def lbe_consistent_step(f, u0, nu: float) -> np.ndarray:
+    """One iteration of the consistent initialisation (Sec. IV.A, after Mei
+    et al.): the MRT-LBE step with the velocity held at u0 (3, nz, ny, nx)."""
+    f = _f64(f)
+    nx, ny, nz = _dims(f)
+    u0 = _f64(u0)
+    if u0.shape != (3, nz, ny, nx):
+        raise ValueError("u0 must have shape (3, nz, ny, nx)")
+    s = _f64(mrt_rates(nu))
+    out = np.empty_like(f)
+    rc = _load().orc_lbe_consistent_step(nx, ny, nz, _ptr(s), _ptr(u0), _ptr(f), _ptr(out))
+    if rc != 0:
+        raise RuntimeError("orc_lbe_consistent_step failed: %d" % rc)
+    return out
+
+
+def lbe_consistent(u0, nu: float, iters: int, drho0=None):
+    """The consistent initial distributions for the velocity u0: iterate
+    lbe_consistent_step from f_eq(drho0, u0) (drho0 = 0 by default) `iters`
+    times.  Returns (f, residuals) with residuals[k] = max |drho^{k+1} -
+    drho^k| over the box."""
+    u0 = _f64(u0)
+    f = equilibrium_field(u0, drho0)
+    res = []
+    d_prev = f.sum(axis=0)
+    for _ in range(iters):
+        f = lbe_consistent_step(f, u0, nu)
+        d = f.sum(axis=0)
+        res.append(float(np.abs(d - d_prev).max()))
+        d_prev = d
+    return f, res
 
 
 def dugks_tau(nu: float) -> float:

@@ -226,6 +226,39 @@ int orc_lbe_step(int nx, int ny, int nz, const double s[Q], const double* fin, d
     return 0;
 }
 
+/* One iteration of the consistent initialisation the paper cites for its
+ * initial distributions (Sec. IV.A; Mei et al. 2006): the LBE step of Eq. 21
+ * with the velocity held at the prescribed u0 ([3][n], rho0 = 1).  The
+ * equilibrium moments take the momentum rho0 u0, and the momentum rows, whose
+ * rate is immaterial in the plain step (they are conserved), relax fully to
+ * it (rate 1); every other row keeps its rate s.  Only the density evolves,
+ * by streaming, until it stops changing. */
+int orc_lbe_consistent_step(int nx, int ny, int nz, const double s[Q], const double* u0, const double* fin,
+                            double* fout) {
+    if (nx <= 0 || ny <= 0 || nz <= 0) return -1;
+    const long n = (long)nx * ny * nz;
+    double M[Q * Q], Minv[Q * Q], sc[Q];
+    orc_mrt_matrix(M);
+    invert(M, Minv, Q);
+    for (int k = 0; k < Q; ++k) sc[k] = s[k];
+    sc[3] = sc[5] = sc[7] = 1.0; /* momentum rows: j_x, j_y, j_z */
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < n; ++c) {
+        int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long)nx * ny));
+        double f[Q], fpost[Q], meq[Q], drho, j[3];
+        for (int i = 0; i < Q; ++i) f[i] = fin[i * n + c];
+        orc_moments(f, &drho, j);
+        orc_mrt_meq(drho, RHO0 * u0[c], RHO0 * u0[n + c], RHO0 * u0[2 * n + c], meq);
+        collide_with(M, Minv, sc, f, meq, fpost);
+        for (int i = 0; i < Q; ++i) {
+            long d = wrap(x + XI[i][0], nx) + (long)nx * (wrap(y + XI[i][1], ny) +
+                                                          (long)ny * wrap(z + XI[i][2], nz));
+            fout[i * n + d] = fpost[i];
+        }
+    }
+    return 0;
+}
+
 /* The paper does not state tau(nu) for DUGKS; the BGK model of Eq. 6 gives
  * nu = tau RT, so tau = nu / RT = 3 nu. */
 double orc_dugks_tau(double nu) { return nu / RT; }
