@@ -66,6 +66,7 @@ def _declare(lib):
         "kin_step": (c_int, [P, c_int]),
         "kin_stats": (c_int, [P, P, P, P]),
         "kin_step_stats": (c_int, [P, c_int, P, P, P]),
+        "kin_init_consistent": (c_int, [P, c_int, ctypes.c_double, P, P]),
         "kin_derived_stats": (c_int, [P, P, P]),
         "kin_num_shells": (c_int, [c_int]),
         "kin_sync": (c_int, [P]),
@@ -199,6 +200,16 @@ class Sim:
     def init_field(self, seed: int, k0: float, re_lambda: float = 0.0):
         _check(lib().kin_init_field(self._h, ctypes.c_uint64(seed), float(k0), float(re_lambda)),
                "kin_init_field")
+
+    def init_consistent(self, max_iter: int = 2000, tol: float = 0.0):
+        """kin_init_consistent (MRT-LBE): iterate with the velocity held
+        fixed until delta-rho changes by <= tol per iteration or max_iter
+        iterations; returns (iterations, last measured change)."""
+        it = ctypes.c_int(0)
+        res = ctypes.c_double(0.0)
+        _check(lib().kin_init_consistent(self._h, int(max_iter), float(tol), ctypes.byref(it), ctypes.byref(res)),
+               "kin_init_consistent")
+        return int(it.value), float(res.value)
 
     def set_velocity(self, u: np.ndarray):
         u = np.ascontiguousarray(u, dtype=np.float64)

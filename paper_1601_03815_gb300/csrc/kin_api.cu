@@ -499,6 +499,52 @@ int kin_step_stats(kin_sim* s, int n, double* E, double* eps, double* Ek) {
     return kin_stats(s, E, eps, Ek);
 }
 
+int kin_init_consistent(kin_sim* s, int max_iter, double tol, int* iters, double* residual) {
+    if (int r = valid(s)) return r;
+    if (s->scheme != KIN_LBE_MRT)
+        return fail(KIN_EINVAL, "the consistent initialisation is the LBE procedure of Sec. IV.A");
+    if (max_iter < 1) return fail(KIN_EINVAL, "max_iter must be >= 1, got %d", max_iter);
+    DeviceGuard g(s->device);
+    if (int r = ensure_u(s)) return r;
+    if (int r = ensure_uh(s)) return r;
+    // u0: the velocity of the current state, held through the iteration
+    CK(velocity_field(s->storage, s->buf[s->cur], shifted(s), s->N, s->u, s->stream));
+    constexpr int kCheckEvery = 10;
+    // scratch: the previous delta-rho (N^3 doubles) in the spectrum buffer,
+    // the largest change in one word of the reduction buffer
+    double* prev = reinterpret_cast<double*>(s->uh);
+    unsigned* maxbits = reinterpret_cast<unsigned*>(s->red);
+    double res = -1.0;
+    int it = 0;
+    while (it < max_iter) {
+        ++it;
+        const bool check = it % kCheckEvery == 0 || it == max_iter;
+        if (check) CK(drho_change(s->storage, s->buf[s->cur], true, s->N, prev, maxbits, 0, s->stream));
+        CK(lbe_consistent_step(s->storage, s->buf[s->cur], s->buf[s->cur ^ 1], s->N, s->nu, s->u, s->stream));
+        s->cur ^= 1;
+        s->launches += 1;
+        if (check) {
+            CK(cudaMemsetAsync(maxbits, 0, sizeof(unsigned), s->stream));
+            CK(drho_change(s->storage, s->buf[s->cur], true, s->N, prev, maxbits, 1, s->stream));
+            unsigned bits = 0;
+            CK(cudaMemcpyAsync(s->h_pin, maxbits, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream));
+            CK(cudaStreamSynchronize(s->stream));
+            std::memcpy(&bits, s->h_pin, sizeof(unsigned));
+            float r;
+            std::memcpy(&r, &bits, sizeof(float));
+            res = r;
+            s->launches += 2;
+            if (!std::isfinite(res)) return fail(KIN_ENONFINITE, "consistent initialisation diverged");
+            if (res <= tol) break;
+        }
+    }
+    s->step = 0;
+    s->epoch += 1;
+    if (iters) *iters = it;
+    if (residual) *residual = res;
+    return KIN_OK;
+}
+
 int kin_stats(kin_sim* s, double* E, double* eps, double* Ek) {
     if (int r = valid(s)) return r;
     DeviceGuard g(s->device);

@@ -211,9 +211,12 @@ __device__ __forceinline__ C meq(C drho, C jx, C jy, C jz, C jj) {
 // M is orthogonal, so M^-1 = M^T diag(1/|M_k|^2); rows are even or odd in xi,
 // so the work splits into the pair sums a_p = f_{2p+1} + f_{2p+2} (even rows)
 // and differences b_p = f_{2p+1} - f_{2p+2} (odd rows).
-template <typename C>
-__device__ __forceinline__ void mrt_collide(C (&f)[Q], const MrtRates<C>& r, C& drho_out, C& jx_out,
-                                            C& jy_out, C& jz_out) {
+// FIXJ: the equilibrium takes the prescribed momentum (jfx, jfy, jfz) and the
+// momentum rows relax fully to it (the consistent initialisation, Sec. IV.A);
+// otherwise the cell's own momentum, conserved.
+template <bool FIXJ, typename C>
+__device__ __forceinline__ void mrt_collide_t(C (&f)[Q], const MrtRates<C>& r, C& drho_out, C& jx_out,
+                                              C& jy_out, C& jz_out, C jfx, C jfy, C jfz) {
     C a[NPAIR], b[NPAIR];
 #pragma unroll
     for (int p = 0; p < NPAIR; ++p) {
@@ -225,11 +228,14 @@ __device__ __forceinline__ void mrt_collide(C (&f)[Q], const MrtRates<C>& r, C& 
     const C jx = (b[0] + b[3]) + (b[4] + (b[5] + b[6]));
     const C jy = (b[1] + b[3]) - (b[4] - (b[7] + b[8]));
     const C jz = (b[2] + b[5]) - (b[6] - (b[7] - b[8]));
-    const C jj = jx * jx + jy * jy + jz * jz;
     drho_out = drho;
     jx_out = jx;
     jy_out = jy;
     jz_out = jz;
+    const C jxe = FIXJ ? jfx : jx, jye = FIXJ ? jfy : jy, jze = FIXJ ? jfz : jz;
+    const C jj = jxe * jxe + jye * jye + jze * jze;
+    // FIXJ: (m - m_eq) / |M_k|^2 of the momentum rows at rate 1 (|M_3|^2 = 10)
+    [[maybe_unused]] const C gjx = (jx - jfx) * C(0.1), gjy = (jy - jfy) * C(0.1), gjz = (jz - jfz) * C(0.1);
 
     C ge[NEVEN], go[NODD];
     static_for<0, NEVEN>([&](auto jc) {
@@ -243,7 +249,7 @@ __device__ __forceinline__ void mrt_collide(C (&f)[Q], const MrtRates<C>& r, C& 
             else if constexpr (c == -1) m -= a[P];
             else if constexpr (c != 0) m += C(c) * a[P];
         });
-        ge[J] = rate<K>(r) * (m - meq<K>(drho, jx, jy, jz, jj)) * (C(1) / C(mnorm(K)));
+        ge[J] = rate<K>(r) * (m - meq<K>(drho, jxe, jye, jze, jj)) * (C(1) / C(mnorm(K)));
     });
     static_for<0, NODD>([&](auto jc) {
         constexpr int J = decltype(jc)::value;
@@ -256,7 +262,7 @@ __device__ __forceinline__ void mrt_collide(C (&f)[Q], const MrtRates<C>& r, C& 
             else if constexpr (c == -1) m -= b[P];
             else if constexpr (c != 0) m += C(c) * b[P];
         });
-        go[J] = rate<K>(r) * (m - meq<K>(drho, jx, jy, jz, jj)) * (C(1) / C(mnorm(K)));
+        go[J] = rate<K>(r) * (m - meq<K>(drho, jxe, jye, jze, jj)) * (C(1) / C(mnorm(K)));
     });
     // back transform: df_i = sum_k M_k,i g_k
     {
@@ -285,9 +291,21 @@ __device__ __forceinline__ void mrt_collide(C (&f)[Q], const MrtRates<C>& r, C& 
             else if constexpr (c == -1) o -= go[J];
             else if constexpr (c != 0) o += C(c) * go[J];
         });
+        if constexpr (FIXJ) {
+            // the momentum rows (M_3,5,7 = xi_x, xi_y, xi_z) relaxed with rate 1
+            if constexpr (pair_x(P) != 0) o += C(pair_x(P)) * gjx;
+            if constexpr (pair_y(P) != 0) o += C(pair_y(P)) * gjy;
+            if constexpr (pair_z(P) != 0) o += C(pair_z(P)) * gjz;
+        }
         f[2 * P + 1] -= e + o;
         f[2 * P + 2] -= e - o;
     });
+}
+
+template <typename C>
+__device__ __forceinline__ void mrt_collide(C (&f)[Q], const MrtRates<C>& r, C& drho_out, C& jx_out,
+                                            C& jy_out, C& jz_out) {
+    mrt_collide_t<false>(f, r, drho_out, jx_out, jy_out, jz_out, C(0), C(0), C(0));
 }
 
 // Periodic neighbour of coordinate v in [0, n).

@@ -37,6 +37,15 @@ cudaError_t dugks_make_tmap(void* tmap, const void* base, int N, int tile_y);
 cudaError_t dugks_step_fused(int storage, const void* src, void* dst, int N, double nu, double dt,
                              int tile_y, int zchunk, cudaStream_t stream, float* uvel = nullptr);
 
+// One iteration of the consistent initialisation of an LBE state (pull
+// layout): the step with the momentum held at u0 (FP64 [3][N^3], device).
+cudaError_t lbe_consistent_step(int storage, const void* src, void* dst, int N, double nu, const double* u0,
+                                cudaStream_t stream);
+// delta-rho of a state into prev (mode 0), or max |delta-rho - prev| into
+// *maxbits as float bits (mode 1; *maxbits must start at 0).
+cudaError_t drho_change(int storage, const void* state, bool shifted, int N, double* prev, unsigned* maxbits,
+                        int mode, cudaStream_t stream);
+
 // Compute-type size of the DUGKS scratch element (4 or 8 bytes).
 size_t dugks_scratch_bytes(int storage);
 

@@ -154,6 +154,48 @@ static cudaError_t launch_lbe(const void* src, void* dst, int N, double nu, int 
     return cudaGetLastError();
 }
 
+// One iteration of the consistent initialisation (Sec. IV.A, after Mei et
+// al.): the node update of lbe_node with the momentum held at rho0 u0 (FP64,
+// [3][N^3]); see mrt_collide_t.
+template <typename S>
+__global__ void __launch_bounds__(256) lbe_consistent_kernel(const S* __restrict__ src, S* __restrict__ dst,
+                                                             int N, size_t plane,
+                                                             MrtRates<typename Traits<S>::C> rates,
+                                                             const double* __restrict__ u0) {
+    using C = typename Traits<S>::C;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    C f[Q];
+    lbe_gather<S, false>(src, N, plane, x, y, z, f);
+    const size_t c = (size_t)x + (size_t)N * (y + (size_t)N * z);
+    C drho, jx, jy, jz;
+    mrt_collide_t<true>(f, rates, drho, jx, jy, jz, (C)u0[c], (C)u0[plane + c], (C)u0[2 * plane + c]);
+    lbe_scatter<S>(dst, N, plane, x, y, z, f);
+}
+
+template <typename S>
+static cudaError_t launch_consistent(const void* src, void* dst, int N, double nu, const double* u0,
+                                     cudaStream_t stream) {
+    using C = typename Traits<S>::C;
+    const int bx = N >= 128 ? 128 : ((N + 31) / 32) * 32;
+    dim3 block(bx), grid((N + bx - 1) / bx, N, N);
+    lbe_consistent_kernel<S><<<grid, block, 0, stream>>>((const S*)src, (S*)dst, N, (size_t)N * N * N,
+                                                         lbe_rates<C>(nu), u0);
+    return cudaGetLastError();
+}
+
+cudaError_t lbe_consistent_step(int storage, const void* src, void* dst, int N, double nu, const double* u0,
+                                cudaStream_t stream) {
+    switch (storage) {
+        case ST_F32: return launch_consistent<float>(src, dst, N, nu, u0, stream);
+        case ST_F16: return launch_consistent<__half>(src, dst, N, nu, u0, stream);
+        case ST_BF16: return launch_consistent<__nv_bfloat16>(src, dst, N, nu, u0, stream);
+        case ST_F64: return launch_consistent<double>(src, dst, N, nu, u0, stream);
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t lbe_step(int storage, const void* src, void* dst, int N, double nu, int block_x,
                      cudaStream_t stream) {
     switch (storage) {

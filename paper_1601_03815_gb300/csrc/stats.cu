@@ -633,6 +633,31 @@ __global__ void sample_kernel(const S* __restrict__ st, bool shifted, int N, siz
     out[t] = (double)Traits<S>::load(st + i * plane + stored_index_rt(i, x, y, z, N, shifted));
 }
 
+// delta-rho of every cell (Eq. 8) into prev (mode 0), or (mode 1) the largest
+// |delta-rho - prev| over the box into *maxbits as the bits of a
+// non-negative float (ordered like the values, so atomicMax applies).
+template <typename S>
+__global__ void drho_change_kernel(const S* __restrict__ st, bool shifted, int N, size_t plane,
+                                   double* __restrict__ prev, unsigned* maxbits, int mode) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    float d = 0.0f;
+    if (x < N) {
+        double rho = 0.0;
+        static_for<0, Q>([&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            rho += (double)Traits<S>::load(st + I * plane + stored_index<I>(x, y, z, N, shifted));
+        });
+        const size_t c = (size_t)x + (size_t)N * (y + (size_t)N * z);
+        if (mode == 0) prev[c] = rho;
+        else d = (float)fabs(rho - prev[c]);
+    }
+    if (mode == 1) {
+        for (int o = 16; o > 0; o >>= 1) d = fmaxf(d, __shfl_down_sync(0xffffffffu, d, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(maxbits, __float_as_uint(d));
+    }
+}
+
 __global__ void nonfinite_kernel(const double* __restrict__ v, size_t n, int* flag) {
     bool bad = false;
     for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
@@ -720,6 +745,16 @@ cudaError_t sample_cells(int storage, const void* state, bool shifted, int N, co
 
 cudaError_t scan_nonfinite(const double* v, size_t n, int* flag, cudaStream_t stream) {
     nonfinite_kernel<<<304, 256, 0, stream>>>(v, n, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t drho_change(int storage, const void* state, bool shifted, int N, double* prev, unsigned* maxbits,
+                        int mode, cudaStream_t stream) {
+    int bx;
+    dim3 g = row_grid(N, bx);
+    const size_t plane = (size_t)N * N * N;
+    KIN_DISPATCH(storage, (drho_change_kernel<S><<<g, bx, 0, stream>>>((const S*)state, shifted, N, plane, prev,
+                                                                      maxbits, mode)));
     return cudaGetLastError();
 }
 
