@@ -78,4 +78,9 @@ def test_invalid_arguments_are_rejected_without_a_device(libkin):
     assert libkin.kin_create(32, 1, 0.01, 0.1, 0.5, 9, None, ctypes.byref(h)) == -1
     assert h.value is None
     assert b"DUGKS" in libkin.kin_last_error() or b"storage" in libkin.kin_last_error()
+    # a NULL simulation is rejected by every entry point that takes one
+    d = ctypes.c_double()
+    assert libkin.kin_step(None, 1) == -1
+    assert libkin.kin_step_stats(None, 1, ctypes.byref(d), ctypes.byref(d), None) == -1
+    assert libkin.kin_init_consistent(None, 10, ctypes.c_double(0.0), None, None) == -1
     libkin.kin_destroy(None)  # NULL-safe
