@@ -189,10 +189,14 @@ int kin_energy_dissipation_noalloc(const double* u, int N, double nu, double* ou
 int kin_num_shells(int N);
 
 /* Launch-shape tuning (all values <= 0 keep the current setting):
- *   block_x  LBE: threads per block along x (multiple of 32, <= 1024)
+ *   block_x  LBE: threads per block along x (multiple of 32, <= 1024; with
+ *            FP16/BF16 storage and even N a thread takes 4 cells, or 2
+ *            when N % 4 != 0)
  *   tile_y   DUGKS fused kernel: rows per tile, 4 or 8
  *   zchunk   DUGKS fused kernel: planes each thread block marches through
- *            (default: as many as keep about two thread blocks per SM)
+ *            (default: when a plane's tile columns fill fewer than 1.5
+ *            waves of blocks, the length with the shortest list schedule of
+ *            the grid; otherwise about two waves of blocks)
  *   variant  DUGKS: 0 = fused single launch, f-tilde staged by per-thread
  *            cp.async copies (default); 1 = two launches (pre-step into
  *            scratch, then flux + update); 2 = fused, f-tilde staged by one
