@@ -198,14 +198,11 @@ int kin_num_shells(int N);
  *            waves of blocks, the length with the shortest list schedule of
  *            the grid; otherwise about two waves of blocks)
  *   variant  DUGKS: 0 = fused single launch, f-tilde staged by per-thread
- *            cp.async copies (default); 1 = two launches (pre-step into
- *            scratch, then flux + update); 2 = fused, f-tilde staged by one
- *            tensor-memory-accelerator copy per plane (FP32 storage with
- *            N % 4 == 0, otherwise as 0; bitwise equal to 0)
+ *            cp.async copies two planes ahead (default); 1 = two launches
+ *            (pre-step into scratch, then flux + update)
  * Results do not depend on the launch shape or variant beyond rounding
  * order (the fused and two-launch forms sum the same terms differently).
- * A staging wait of variant 2 that gives up (bounded) makes the next
- * kin_sync or kin_stats return KIN_ETIMEOUT. */
+ * Other variant values return KIN_EINVAL. */
 int kin_set_tuning(kin_sim* sim, int block_x, int tile_y, int zchunk, int variant);
 
 /* Number of kernel launches one kin_step(sim, 1) enqueues. */

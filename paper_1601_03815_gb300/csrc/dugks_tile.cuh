@@ -5,7 +5,8 @@
 // of planes.  Its 32 x (TY + 2) threads cover the columns plus a one-cell halo;
 // every thread runs the cell pre-step (Eq. 19) of its own column for the next
 // plane into a three-plane ring of f-bar-plus in shared memory, fed by
-// cp.async copies of f-tilde issued two planes ahead.
+// cp.async copies of f-tilde issued two planes ahead.  Two block barriers per
+// plane: after the pre-step, and before the y faces.
 //
 // Interface reconstruction splits exactly between the two cells of a face.
 // With G_i^t(X) = fbp_i(X + e_t) - fbp_i(X - e_t) the Eq. 13/15/16 value at the
@@ -19,8 +20,9 @@
 // face plus density and momentum); a face (Eqs. 17, 7, 18, 10) needs one
 // record from each neighbour: x neighbours exchange records by warp shuffles,
 // y neighbours through shared memory, z neighbours are the same thread one
-// plane apart.  Updates lag one plane so the z face uses one cell view per
-// plane.
+// plane apart.
+//
+// Updates lag one plane so the z face uses one cell view per plane.
 //
 // Opposite populations (2p+1, 2p+2) travel as one pair (pair_math.cuh): both
 // always undergo the same operation with a fixed coefficient pattern, so one
@@ -28,8 +30,6 @@
 // Dhat_p = (D_{2p+1}, -D_{2p+2}), so a face adds the same signed value to
 // both members.
 #pragma once
-
-#include <cuda.h>
 
 #include <type_traits>
 
@@ -102,13 +102,15 @@ struct FusedSmem {
     C mym[4][TY + 2][32];              // y-face M records (density, momentum)
 };
 
-// Raw f-tilde staging for FP32 storage, filled by cp.async: planes z - 1 and z
-// (awaiting their update), z + 1 (next pre-step) and z + 2 (in flight while
-// plane z is computed).  Other storage types read global memory directly.
+// Raw f-tilde staging for FP32 storage, filled by per-thread 4-byte cp.async
+// copies: planes z - 1 and z (awaiting their update), z + 1 (next pre-step)
+// and z + 2 (in flight while plane z is computed).  One population per
+// 128-byte row, so a warp's copy fills one row without bank conflicts and
+// touches one population plane; the pre-step and update read the two members
+// of a pair with two 4-byte loads.  FP64 storage reads global memory directly.
 template <int TY>
 struct RawStage {
-    float2 raw[4][NPAIR][TY + 2][32];
-    float raw0[4][TY + 2][32];
+    float raw[4][Q][TY + 2][32];
 };
 
 template <typename S>
@@ -137,69 +139,6 @@ __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-// Raw staging by the tensor-memory accelerator (FP32, N a multiple of 4): one
-// cp.async.bulk.tensor per plane copies the box x = xs .. xs + 35 (xs = x0 - 1
-// rounded down to a multiple of 4, so the copy starts on a 16-byte boundary),
-// rows y0 - 1 .. y0 + TY, all 19 populations into a slot laid out
-// [population][row][36]; thread `lane` reads element lane + (x0 - 1 - xs).
-// Cells outside the box's periodic image (a tile at the domain edge) arrive
-// as zeros and are patched by their own thread with plain loads.  Each slot
-// has an mbarrier that completes once per copy.
-constexpr int TMA_W = 36;
-template <int TY>
-constexpr int tma_slot_floats() {
-    return ((Q * (TY + 2) * TMA_W + 31) / 32) * 32;  // 128-byte multiple
-}
-template <int TY>
-struct TmaStage {
-    float raw[4][tma_slot_floats<TY>()];
-    unsigned long long bar[4];
-};
-template <int TY>
-constexpr unsigned tma_box_bytes() {
-    return (unsigned)(Q * (TY + 2) * TMA_W * sizeof(float));
-}
-
-__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* b, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(b)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_addr(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                            unsigned long long* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-        "[%6];\n" ::"r"(smem_addr(dst)),
-        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
-        : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
-
-// Iterations of a bounded mbarrier wait before the kernel gives up, records
-// the failure and carries on with whatever the slot holds; after one failure a
-// thread no longer waits, so a lost copy costs one limit, not one per plane.
-constexpr long long TMA_WAIT_LIMIT = 1ll << 20;
-
-template <typename S, int TY, bool TMA = false>
-constexpr size_t fused_smem_bytes_v() {
-    using C = typename Traits<S>::C;
-    if constexpr (TMA) return sizeof(FusedSmem<C, TY>) + sizeof(TmaStage<TY>);
-    else return sizeof(FusedSmem<C, TY>) + (kAsyncStage<S> ? sizeof(RawStage<TY>) : kStage16<S> ? sizeof(RawStage16<S, TY>) : 0);
-}
 
 template <typename S, int TY>
 constexpr size_t fused_smem_bytes() {
@@ -369,25 +308,20 @@ __device__ __forceinline__ int wrapc(int v, int n) {
 
 // ------------------------------------------------------------------ the tile
 // One tile (tile coordinates bx, by, bz) of the fused step, run by a
-// 32 x (TY + 2) thread block with fused_smem_bytes_v<S, TY, TMA>() of dynamic
-// shared memory at smem_raw (128-byte aligned for TMA).  Also called by the
-// persistent ensemble kernel (without TMA).  With TMA (FP32, N % 4 == 0),
-// tmap describes src as a 4-D tensor (x, y, z, population) with a box of
-// TMA_W x (TY + 2) x 1 x 19, and a wait that exceeds TMA_WAIT_LIMIT sets *err.
-// With VEL (FP32-computed storage) the tile also writes rho0 u = sum xi f of
-// the stored new state (Eq. 8) to uvel[3][N^3], summed in population order.
-template <typename S, int TY, bool TMA = false, bool VEL = false>
+// 32 x (TY + 2) thread block with fused_smem_bytes<S, TY>() of dynamic shared
+// memory at smem_raw (16-byte aligned).  Also called by the persistent
+// ensemble kernel.  With VEL (FP32-computed storage) the tile also writes
+// rho0 u = sum xi f of the stored new state (Eq. 8) to uvel[3][N^3], summed in
+// population order.
+template <typename S, int TY, bool VEL = false>
 __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restrict__ dst, int N,
                                            int bx, int by, int bz, int zchunk,
                                            const DugksCoef<typename Traits<S>::C>& kc,
-                                           unsigned char* smem_raw, const CUtensorMap* tmap = nullptr,
-                                           int* err = nullptr, float* __restrict__ uvel = nullptr) {
+                                           unsigned char* smem_raw, float* __restrict__ uvel = nullptr) {
     using C = typename Traits<S>::C;
     using P2 = Pr<C>;
-    static_assert(!TMA || std::is_same<S, float>::value, "TMA staging is for FP32 storage");
     static_assert(!VEL || std::is_same<C, float>::value, "the fused velocity serves FP32-computed storage");
     FusedSmem<C, TY>& sm = *reinterpret_cast<FusedSmem<C, TY>*>(smem_raw);
-    TmaStage<TY>* tst = reinterpret_cast<TmaStage<TY>*>(smem_raw + sizeof(FusedSmem<C, TY>));
     RawStage<TY>* stage = reinterpret_cast<RawStage<TY>*>(smem_raw + sizeof(FusedSmem<C, TY>));
     RawStage16<S, TY>* stage16 = reinterpret_cast<RawStage16<S, TY>*>(smem_raw + sizeof(FusedSmem<C, TY>));
 
@@ -410,32 +344,12 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
     auto zwrap = [&](int z) { return z < 0 ? z + N : (z >= N ? z - N : z); };
     auto rslot_of = [&](int z) { return (z - z0 + 4) & 3; };
 
-    // TMA staging geometry: box start xs (a multiple of 4), this lane's offset
-    // in the box row, and whether this thread's cell lies outside the box's
-    // unwrapped image (patched with plain loads after every copy)
-    const int xs = x0 - 1 - (((x0 - 1) % 4) + 4) % 4;
-    const int tma_off = x0 - 1 - xs;
-    const bool tma_patch = gxr < 0 || gxr >= N || gyr < 0 || gyr >= N;
-    bool tma_timed_out = false;
-    auto tslot = [&](int z) { return (z - z0 + 1) & 3; };
-    auto tparity = [&](int z) { return (unsigned)(((z - z0 + 1) >> 2) & 1); };
-    auto traw = [&](int s, int i) -> float& { return tst->raw[s][(i * (TY + 2) + row) * TMA_W + lane + tma_off]; };
-
     // 2-byte staging: this lane's word starts at element x0 - 2 + 2 lane (even,
     // so it never straddles the wrap when N is even)
     const bool use16 = kStage16<S> && (N % 2 == 0);
     const size_t rowidx = (size_t)N * gy + (size_t)wrapc(x0 - 2 + 2 * lane, N);
 
     auto issue_plane = [&](int z) {
-        if constexpr (TMA) {
-            if (z <= zend && threadIdx.x == 0 && threadIdx.y == 0) {
-                const int s = tslot(z);
-                fence_proxy_async();  // earlier generic accesses to the slot precede the copy
-                mbar_arrive_expect_tx(&tst->bar[s], tma_box_bytes<TY>());
-                tma_load_4d(&tst->raw[s][0], tmap, xs, y0 - 1, zwrap(z), 0, &tst->bar[s]);
-            }
-            return;
-        }
         if constexpr (kStage16<S>) {
             if (use16) {
                 if (lane <= 16) {
@@ -450,21 +364,15 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
         if constexpr (kAsyncStage<S>) {
             const S* p = src + (size_t)zwrap(z) * nn + colidx;
             const int s = rslot_of(z);
-            cp_async4(&stage->raw0[s][row][lane], p);
 #pragma unroll
-            for (int q = 0; q < NPAIR; ++q) {
-                cp_async4(&stage->raw[s][q][row][lane].x, p + (2 * q + 1) * plane);
-                cp_async4(&stage->raw[s][q][row][lane].y, p + (2 * q + 2) * plane);
-            }
+            for (int i = 0; i < Q; ++i) cp_async4(&stage->raw[s][i][row][lane], p + i * plane);
             cp_async_commit();
         }
     };
     auto raw_pair = [&](int z, int q) -> P2 {
-        if constexpr (TMA) {
-            const int s = tslot(z);
-            return pmk(traw(s, 2 * q + 1), traw(s, 2 * q + 2));
-        } else if constexpr (kAsyncStage<S>) {
-            return stage->raw[rslot_of(z)][q][row][lane];
+        if constexpr (kAsyncStage<S>) {
+            const int s = rslot_of(z);
+            return pmk(stage->raw[s][2 * q + 1][row][lane], stage->raw[s][2 * q + 2][row][lane]);
         } else {
             if constexpr (kStage16<S>) {
                 if (use16) {
@@ -478,10 +386,8 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
         }
     };
     auto raw_rest = [&](int z) -> C {
-        if constexpr (TMA) {
-            return traw(tslot(z), 0);
-        } else if constexpr (kAsyncStage<S>) {
-            return stage->raw0[rslot_of(z)][row][lane];
+        if constexpr (kAsyncStage<S>) {
+            return stage->raw[rslot_of(z)][0][row][lane];
         } else {
             if constexpr (kStage16<S>) {
                 if (use16) return to_float(stage16->raw[rslot_of(z)][0][row][lane + 1]);
@@ -556,42 +462,9 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
         cp_async_wait_all();
         if constexpr (kStage16<S>) __syncwarp();
     };
-    // TMA: wait (bounded) for the copy of plane z, then patch this thread's
-    // cell if the box held it only as a zero-filled out-of-range element
-    auto wait_plane = [&](int z) {
-        if constexpr (TMA) {
-            const int s = tslot(z);
-            long long n = 0;
-            while (!tma_timed_out && !mbar_try_wait(&tst->bar[s], tparity(z))) {
-                if (++n > TMA_WAIT_LIMIT) {
-                    tma_timed_out = true;
-                    if (err) atomicExch(err, 1);
-                }
-            }
-            if (tma_patch) {
-                const S* p = src + (size_t)zwrap(z) * nn + colidx;
-#pragma unroll
-                for (int i = 0; i < Q; ++i) traw(s, i) = Traits<S>::load(p + i * plane);
-            }
-        }
-    };
-
-    if constexpr (TMA) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) mbar_init(&tst->bar[k], 1);
-            fence_mbar_init();
-        }
-        __syncthreads();
-    }
     issue_plane(z0 - 1);
     issue_plane(z0);
-    if constexpr (TMA) {
-        wait_plane(z0 - 1);
-        wait_plane(z0);
-    } else {
-        wait_copies();
-    }
+    wait_copies();
     prestep(z0 - 1, s_m1);
     prestep(z0, s_0);
     issue_plane(z0 + 1);
@@ -615,8 +488,7 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
     for (int z = z0; z <= zend; ++z) {
         const bool last = z == zend;
         if (!last) {
-            if constexpr (TMA) wait_plane(z + 1);
-            else if constexpr (kAsyncStage<S> || kStage16<S>) wait_copies();
+            if constexpr (kAsyncStage<S> || kStage16<S>) wait_copies();
             prestep(z + 1, s_p1);
             if (z + 2 <= zend) issue_plane(z + 2);
         }
@@ -757,19 +629,6 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
         s_m1 = s_0;
         s_0 = s_p1;
         s_p1 = st;
-    }
-    if constexpr (TMA) {
-        // after a wait that gave up, wait (bounded) once more for the last
-        // copy into each slot before the block's shared memory is released
-        if (tma_timed_out) {
-            for (int k = 0; k < 4; ++k) {
-                const int zl = zend - ((tslot(zend) - k + 4) & 3);
-                long long n = 0;
-                if (zl >= z0 - 1)
-                    while (!mbar_try_wait(&tst->bar[k], tparity(zl)) && ++n <= TMA_WAIT_LIMIT) {
-                    }
-            }
-        }
     }
 }
 

@@ -135,8 +135,14 @@ double dugks_makespan(int N, long long cols, int zc, int nsm) {
 // two waves of blocks, rounded down to 8 planes: at 256^3 that is 240 + 16
 // planes, the measured optimum, which the schedule model (blind to cache
 // effects) misranks by ~1 %.
+// Rows per fused-DUGKS tile actually launched for this simulation's tuning.
+int fused_tile_y(const kin_sim* s) {
+    if (s->storage == ST_F64) return 4;
+    return s->tile_y == 4 ? 4 : 8;
+}
+
 int auto_zchunk(kin_sim* s) {
-    const int ty = s->storage == ST_F64 ? 4 : (s->tile_y == 4 ? 4 : 8);
+    const int ty = fused_tile_y(s);
     if (s->zc_auto > 0 && s->zc_auto_ty == ty) return s->zc_auto;
     const int N = s->N;
     const long long cols = (long long)((N + 29) / 30) * ((N + ty - 1) / ty);
@@ -163,21 +169,6 @@ int auto_zchunk(kin_sim* s) {
     return best_zc;
 }
 
-// Tensor maps for the TMA-staged DUGKS step; the cp.async path is used when
-// they cannot be made (FP16/BF16/FP64 storage, N % 4 != 0, no encoder).
-void refresh_tmaps(kin_sim* s) {
-    s->tma_ok = false;
-    if (s->scheme != KIN_DUGKS || s->storage != ST_F32 || s->N % 4 != 0) return;
-    const int ty = s->tile_y == 4 ? 4 : 8;
-    for (int k = 0; k < 2; ++k)
-        if (dugks_make_tmap(s->tmap[k], s->buf[k], s->N, ty) != cudaSuccess) {
-            cudaGetLastError();
-            return;
-        }
-    s->tmap_ty = ty;
-    s->tma_ok = true;
-}
-
 // KIN_ETIMEOUT (and clear the flag) if a kernel of this simulation gave up a
 // bounded wait; call after the stream is synchronised.
 int check_device_error(kin_sim* s) {
@@ -185,7 +176,7 @@ int check_device_error(kin_sim* s) {
     CK(cudaMemcpy(&flag, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag) {
         CK(cudaMemset(s->d_err, 0, sizeof(int)));
-        return fail(KIN_ETIMEOUT, "a staging wait gave up in a DUGKS step; the state is not valid");
+        return fail(KIN_ETIMEOUT, "a kernel of this simulation reported an error; the state is not valid");
     }
     return KIN_OK;
 }
@@ -193,7 +184,7 @@ int check_device_error(kin_sim* s) {
 // The step goes to the fused cp.async DUGKS kernel, which can also write the
 // new state's velocity (FP32-computed storage).
 bool fused_velocity_ok(const kin_sim* s) {
-    return s->scheme == KIN_DUGKS && s->storage != ST_F64 && s->variant != 1 && !(s->variant == 2 && s->tma_ok);
+    return s->scheme == KIN_DUGKS && s->storage != ST_F64 && s->variant != 1;
 }
 
 // One step; with uvel (only where fused_velocity_ok) the step also leaves the
@@ -206,9 +197,6 @@ int launch_step(kin_sim* s, float* uvel = nullptr) {
         e = lbe_step(s->storage, src, dst, s->N, s->nu, s->block_lbe, s->stream);
     else if (s->variant == 1)
         e = dugks_step(s->storage, src, dst, s->fbp, s->N, s->nu, s->dt, s->block_dugks, s->stream);
-    else if (s->variant == 2 && s->tma_ok)
-        e = dugks_step_fused_tma(s->tmap[s->cur], src, dst, s->N, s->nu, s->dt, s->tmap_ty,
-                                 s->zchunk > 0 ? s->zchunk : auto_zchunk(s), s->d_err, s->stream);
     else
         e = dugks_step_fused(s->storage, src, dst, s->N, s->nu, s->dt, s->tile_y,
                              s->zchunk > 0 ? s->zchunk : auto_zchunk(s), s->stream, uvel);
@@ -304,7 +292,6 @@ int kin_create(int N, int scheme, double nu, double Ma, double dt, int storage, 
         e = cudaMallocHost(&s->h_pin, 4 * sizeof(double));
         if (e != cudaSuccess) return bail(fail(KIN_ENOMEM, "pinned words: %s", cudaGetErrorString(e)));
     }
-    refresh_tmaps(s);
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return bail(fail(KIN_ECUDA, "sync: %s", cudaGetErrorString(e)));
     *out = s;
@@ -692,18 +679,14 @@ int kin_set_tuning(kin_sim* s, int block_x, int tile_y, int zchunk, int variant)
     if (int r = valid(s)) return r;
     if (block_x > 0 && (block_x % 32 || block_x > 1024)) return fail(KIN_EINVAL, "block_x %d", block_x);
     if (tile_y > 0 && tile_y != 4 && tile_y != 8) return fail(KIN_EINVAL, "tile_y must be 4 or 8");
-    if (variant > 2) return fail(KIN_EINVAL, "variant %d", variant);
+    if (variant > 1) return fail(KIN_EINVAL, "variant %d", variant);
     if (variant == 1 && s->scheme == KIN_DUGKS && !s->fbp) {
         const size_t fb = Q * ncell(s) * dugks_scratch_bytes(s->storage);
         DeviceGuard g(s->device);
         CK(cudaMalloc(&s->fbp, fb));
     }
     if (block_x > 0) s->block_lbe = s->block_dugks = block_x;
-    if (tile_y > 0 && tile_y != s->tile_y) {
-        s->tile_y = tile_y;
-        DeviceGuard g(s->device);
-        refresh_tmaps(s);
-    }
+    if (tile_y > 0) s->tile_y = tile_y;
     if (zchunk > 0) s->zchunk = zchunk;
     if (variant >= 0) s->variant = variant;
     return KIN_OK;

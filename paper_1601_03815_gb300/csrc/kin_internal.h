@@ -26,12 +26,6 @@ cudaError_t dugks_step(int storage, const void* src, void* dst, void* fbp, int N
 
 // Fused single-launch DUGKS step; tile_y in {4, 8} (FP64 always uses 4),
 // zchunk planes per CTA.
-// TMA-staged fused DUGKS step for FP32 storage with N % 4 == 0: tmap is a
-// tensor map of src made by dugks_make_tmap (64 bytes, 64-byte aligned);
-// *err is set if a staging wait gives up.
-cudaError_t dugks_step_fused_tma(const void* tmap, const void* src, void* dst, int N, double nu, double dt,
-                                 int tile_y, int zchunk, int* err, cudaStream_t stream);
-cudaError_t dugks_make_tmap(void* tmap, const void* base, int N, int tile_y);
 // uvel: NULL, or (FP32-computed storage) uvel[3][N^3] receives the velocity
 // of the new state, bitwise equal to velocity_field32 of it.
 cudaError_t dugks_step_fused(int storage, const void* src, void* dst, int N, double nu, double dt,

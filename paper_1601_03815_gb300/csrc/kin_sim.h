@@ -28,11 +28,6 @@ struct kin_sim {
     int block_lbe = 0, block_dugks = 0;
     int tile_y = 8, zchunk = 0, variant = 0;  // zchunk 0: chosen per launch
     int zc_auto = 0, zc_auto_ty = 0;  // the chosen z chunk and the tile height it was chosen for
-    // TMA staging of the fused DUGKS step (FP32, N % 4 == 0): tensor maps of
-    // buf[0] and buf[1] for the current tile_y (CUtensorMap, 128 bytes each)
-    alignas(64) unsigned char tmap[2][128] = {};
-    bool tma_ok = false;
-    int tmap_ty = 0;
     int* d_err = nullptr;  // set by a kernel whose bounded wait gave up
     double* h_pin = nullptr;  // pinned host words: E, eps, and the error flag
     int64_t launches = 0;  // own kernel launches

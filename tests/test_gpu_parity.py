@@ -40,7 +40,7 @@ def _scheme(kin, name):
     return kin.LBE_MRT if name == "lbe" else kin.DUGKS
 
 
-@pytest.mark.parametrize("scheme", ["lbe", "dugks", "dugks-split", "dugks-ty4", "dugks-tma"])
+@pytest.mark.parametrize("scheme", ["lbe", "dugks", "dugks-split", "dugks-ty4"])
 @pytest.mark.parametrize("storage", [3, 0, 1, 2])
 @pytest.mark.parametrize("N", [2, 5, 12, 33, 36])
 def test_one_step_parity(kin, orc, scheme, storage, N):
@@ -51,8 +51,6 @@ def test_one_step_parity(kin, orc, scheme, storage, N):
         sim.set_tuning(variant=1)
     elif scheme == "dugks-ty4":
         sim.set_tuning(tile_y=4, zchunk=3)
-    elif scheme == "dugks-tma":
-        sim.set_tuning(variant=2)  # TMA staging where it applies (FP32, N % 4 == 0)
     scheme = scheme.split("-")[0]
     sim.set_f(f0)
     f_in = sim.get_f()  # the stored (rounded) state is what the GPU steps from
@@ -65,19 +63,19 @@ def test_one_step_parity(kin, orc, scheme, storage, N):
     sim.close()
 
 
-@pytest.mark.parametrize("scheme", ["lbe", "dugks", "dugks-ty4", "dugks-tma"])
+@pytest.mark.parametrize("scheme", ["lbe", "dugks", "dugks-ty4", "dugks-zc"])
 def test_one_step_parity_ragged_large(kin, orc, scheme):
     """Sizes spanning several thread blocks and z chunks with ragged tails
-    (x tiles of 30 and 128, y tiles of 4 and 8, z chunks of 32 and 7)."""
-    # 68: the TMA-staged path (N % 4 == 0) with ragged x and y tiles
-    N = 130 if scheme == "lbe" else (68 if scheme == "dugks-tma" else 67)
+    (x tiles of 30 and 128, y tiles of 4 and 8, z chunks of 7, 11 and the
+    default)."""
+    N = 130 if scheme == "lbe" else (68 if scheme == "dugks-zc" else 67)
     nu, dt = 0.02, (1.0 if scheme == "lbe" else 0.35355)
     f0 = _state(orc, N, 5)
     sim = kin.Sim(N, _scheme(kin, scheme), nu, 0.1, dt, kin.F32)
     if scheme == "dugks-ty4":
         sim.set_tuning(tile_y=4, zchunk=7)
-    elif scheme == "dugks-tma":
-        sim.set_tuning(variant=2, zchunk=11)
+    elif scheme == "dugks-zc":
+        sim.set_tuning(zchunk=11)
     scheme = scheme.split("-")[0]
     sim.set_f(f0)
     sim.step(1)
