@@ -32,6 +32,7 @@ _lock = threading.Lock()
 _lib = None
 
 Q = 19
+RHO0 = 1.0  # reference density (lattice units, Sec. IV.A)
 
 
 def build(force: bool = False) -> str:
@@ -201,6 +202,38 @@ def lbe_consistent(u0, nu: float, iters: int, drho0=None):
     d_prev = f.sum(axis=0)
     for _ in range(iters):
         f = lbe_consistent_step(f, u0, nu)
+        d = f.sum(axis=0)
+        res.append(float(np.abs(d - d_prev).max()))
+        d_prev = d
+    return f, res
+
+
+def dugks_consistent_step(f, u0, nu: float, dt: float) -> np.ndarray:
+    """One iteration of the consistent initialisation for DUGKS (Sec. IV.A:
+    "as for the LBE and DUGKS methods", after Mei et al.): the DUGKS step of
+    Eqs. 9-20, after which the momentum of the new f-tilde is set back to
+    rho0 u0 along the linear term of the equilibrium (Eq. 7),
+    f-tilde_i += 3 W_i xi_i . rho0 (u0 - u), which changes neither the mass
+    nor the second moment.  The density evolves freely."""
+    xi, w = lattice()
+    u0 = _f64(u0)
+    g = dugks_step(f, nu, dt)
+    _, u = macro(g)
+    du = RHO0 * (u0 - u)
+    g += 3.0 * w[:, None, None, None] * np.einsum("ia,azyx->izyx", xi.astype(np.float64), du)
+    return g
+
+
+def dugks_consistent(u0, nu: float, dt: float, iters: int, drho0=None):
+    """The consistent initial distributions for DUGKS: iterate
+    dugks_consistent_step from f_eq(drho0, u0) `iters` times.  Returns
+    (f, residuals), residuals[k] = max |drho^{k+1} - drho^k|."""
+    u0 = _f64(u0)
+    f = equilibrium_field(u0, drho0)
+    res = []
+    d_prev = f.sum(axis=0)
+    for _ in range(iters):
+        f = dugks_consistent_step(f, u0, nu, dt)
         d = f.sum(axis=0)
         res.append(float(np.abs(d - d_prev).max()))
         d_prev = d

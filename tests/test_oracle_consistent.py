@@ -57,3 +57,41 @@ def test_plain_steps_do_not_give_the_pressure(orc):
     for _ in range(200):
         f = orc.lbe_step(f, NU)
     assert np.abs(f.sum(axis=0) - exact).max() / np.abs(exact).max() > 0.3
+
+
+# DUGKS (Sec. IV.A applies the procedure to both schemes): a plain DUGKS step
+# followed by the momentum set back to rho0 u0 along the equilibrium's linear
+# term.  The same Poisson pressure pins it.
+DT = 0.5
+
+
+def test_dugks_taylor_green_pressure_at_second_order(orc):
+    errs = []
+    for N, iters in ((16, 1200), (32, 3000)):
+        u, exact = _tg(N)
+        f, res = orc.dugks_consistent(u, NU, DT, iters)
+        d = f.sum(axis=0)
+        assert res[-1] < 1e-13  # converged
+        assert abs(d.mean()) < 1e-14  # mass is conserved (rounding over the iterations)
+        errs.append(np.abs(d - exact).max() / np.abs(exact).max())
+    assert errs[1] < 0.025, errs
+    assert errs[0] / errs[1] > 3.5, errs
+
+
+def test_dugks_velocity_is_held_and_uniform_flow_keeps_uniform_density(orc):
+    u, _ = _tg(16)
+    f, _ = orc.dugks_consistent(u, NU, DT, 50)
+    _, um = orc.macro(f)
+    assert np.abs(um - u).max() < 1e-15  # the reset makes the momentum exactly rho0 u0
+    uni = np.zeros((3, 2, 3, 4))
+    uni[0], uni[1], uni[2] = 0.03, -0.01, 0.02
+    f, res = orc.dugks_consistent(uni, NU, DT, 20)
+    assert np.abs(f.sum(axis=0)).max() < 1e-15 and max(res) < 1e-15
+
+
+def test_dugks_plain_steps_do_not_give_the_pressure(orc):
+    u, exact = _tg(16)
+    f = orc.equilibrium_field(u)
+    for _ in range(400):
+        f = orc.dugks_step(f, NU, DT)
+    assert np.abs(f.sum(axis=0) - exact).max() / np.abs(exact).max() > 0.3
