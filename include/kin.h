@@ -104,21 +104,24 @@ int kin_sample_f(kin_sim* sim, const int64_t* cells, int64_t n, double* out);
  * Synchronous. */
 int kin_get_velocity(kin_sim* sim, double* u);
 
-/* Consistent initial distributions of an MRT-LBE simulation (Sec. IV.A: the
- * paper's LBE and DUGKS runs start from distributions that carry the initial
- * pressure and the non-equilibrium part, obtained by the iteration of Mei et
- * al.).  The velocity u0 of the current state (as set by kin_init_field or
- * kin_set_velocity) is held fixed while LBE steps repeat: the equilibrium
- * takes the momentum rho0 u0 and the momentum rows relax fully to it, the
- * other rows with the Sec. IV.A rates, so only the density evolves, towards
- * c_s^2 lap(delta-rho) = -d_a d_b (u0_a u0_b).  Every 10 iterations (and at
- * the last) the change of delta-rho over one iteration, max over the box, is
- * measured; the iteration stops when it is <= tol or after max_iter >= 1
- * iterations.  *iters (may be NULL) receives the iterations done, *residual
- * (may be NULL) the last measured change.  The state then holds the result
- * as the state at step 0.  Synchronous.  KIN_EINVAL for a DUGKS simulation
- * (the procedure is the LBE's) or max_iter < 1; KIN_ENONFINITE if it
- * diverges. */
+/* Consistent initial distributions (Sec. IV.A: the paper's LBE and DUGKS
+ * runs start from distributions that carry the initial pressure and the
+ * non-equilibrium part, obtained by the iteration of Mei et al.).  The
+ * velocity u0 of the current state (as set by kin_init_field or
+ * kin_set_velocity) is held fixed while steps repeat, so only the density
+ * evolves, towards c_s^2 lap(delta-rho) = -d_a d_b (u0_a u0_b):
+ *   MRT-LBE: the equilibrium takes the momentum rho0 u0 and the momentum
+ *            rows relax fully to it, the other rows with the Sec. IV.A rates;
+ *   DUGKS:   a plain step (Eqs. 9-20), after which the momentum of f-tilde
+ *            returns to rho0 u0 along the linear term of the equilibrium,
+ *            f_i += 3 W_i xi_i . rho0 (u0 - u) (the mass and the second
+ *            moment unchanged).
+ * Every 10 iterations (and at the last) the change of delta-rho over one
+ * iteration, max over the box, is measured; the iteration stops when it is
+ * <= tol or after max_iter >= 1 iterations.  *iters (may be NULL) receives the
+ * iterations done, *residual (may be NULL) the last measured change.  The
+ * state then holds the result as the state at step 0.  Synchronous.
+ * KIN_EINVAL for max_iter < 1; KIN_ENONFINITE if it diverges. */
 int kin_init_consistent(kin_sim* sim, int max_iter, double tol, int* iters, double* residual);
 
 /* Enqueue n >= 0 time steps on the simulation's stream and return. */

@@ -202,8 +202,8 @@ class Sim:
                "kin_init_field")
 
     def init_consistent(self, max_iter: int = 2000, tol: float = 0.0):
-        """kin_init_consistent (MRT-LBE): iterate with the velocity held
-        fixed until delta-rho changes by <= tol per iteration or max_iter
+        """kin_init_consistent (MRT-LBE or DUGKS): iterate with the velocity
+        held fixed until delta-rho changes by <= tol per iteration or max_iter
         iterations; returns (iterations, last measured change)."""
         it = ctypes.c_int(0)
         res = ctypes.c_double(0.0)

@@ -127,4 +127,52 @@ cudaError_t dugks_step(int storage, const void* src, void* dst, void* fbp, int N
     return cudaErrorInvalidValue;
 }
 
+// The momentum reset of one iteration of the consistent initialisation for
+// DUGKS (Sec. IV.A, after Mei et al.): after a plain DUGKS step the momentum of
+// f-tilde returns to rho0 u0 along the linear term of the equilibrium (Eq. 7),
+// f_i += 3 W_i xi_i . rho0 (u0 - u), in place; the mass and the second
+// moment are unchanged.
+template <typename S>
+__global__ void __launch_bounds__(256)
+    dugks_reset_momentum_kernel(S* __restrict__ f, int N, size_t plane, const double* __restrict__ u0) {
+    using C = typename Traits<S>::C;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    const size_t c = (size_t)x + (size_t)N * (blockIdx.y + (size_t)N * blockIdx.z);
+    C v[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v[i] = Traits<S>::load(f + i * plane + c);
+    C drho, jx, jy, jz;
+    moments(v, drho, jx, jy, jz);
+    // rho0 = 1
+    const C dx = C(u0[c]) - jx, dy = C(u0[plane + c]) - jy, dz = C(u0[2 * plane + c]) - jz;
+    static_for<1, Q>([&](auto ic) {
+        constexpr int I = decltype(ic)::value;
+        constexpr int X = cx(I), Y = cy(I), Z = cz(I);
+        C xd = C(0);
+        if constexpr (X != 0) xd += C(X) * dx;
+        if constexpr (Y != 0) xd += C(Y) * dy;
+        if constexpr (Z != 0) xd += C(Z) * dz;
+        Traits<S>::store(f + I * plane + c, v[I] + lin3w<C>(X * X + Y * Y + Z * Z) * xd);
+    });
+}
+
+template <typename S>
+static cudaError_t launch_reset(void* f, int N, const double* u0, cudaStream_t stream) {
+    const int bx = N >= 128 ? 128 : ((N + 31) / 32) * 32;
+    dim3 block(bx), grid((N + bx - 1) / bx, N, N);
+    dugks_reset_momentum_kernel<S><<<grid, block, 0, stream>>>((S*)f, N, (size_t)N * N * N, u0);
+    return cudaGetLastError();
+}
+
+cudaError_t dugks_reset_momentum(int storage, void* f, int N, const double* u0, cudaStream_t stream) {
+    switch (storage) {
+        case ST_F32: return launch_reset<float>(f, N, u0, stream);
+        case ST_F16: return launch_reset<__half>(f, N, u0, stream);
+        case ST_BF16: return launch_reset<__nv_bfloat16>(f, N, u0, stream);
+        case ST_F64: return launch_reset<double>(f, N, u0, stream);
+    }
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace kin

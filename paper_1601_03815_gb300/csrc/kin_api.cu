@@ -488,8 +488,6 @@ int kin_step_stats(kin_sim* s, int n, double* E, double* eps, double* Ek) {
 
 int kin_init_consistent(kin_sim* s, int max_iter, double tol, int* iters, double* residual) {
     if (int r = valid(s)) return r;
-    if (s->scheme != KIN_LBE_MRT)
-        return fail(KIN_EINVAL, "the consistent initialisation is the LBE procedure of Sec. IV.A");
     if (max_iter < 1) return fail(KIN_EINVAL, "max_iter must be >= 1, got %d", max_iter);
     DeviceGuard g(s->device);
     if (int r = ensure_u(s)) return r;
@@ -506,13 +504,20 @@ int kin_init_consistent(kin_sim* s, int max_iter, double tol, int* iters, double
     while (it < max_iter) {
         ++it;
         const bool check = it % kCheckEvery == 0 || it == max_iter;
-        if (check) CK(drho_change(s->storage, s->buf[s->cur], true, s->N, prev, maxbits, 0, s->stream));
-        CK(lbe_consistent_step(s->storage, s->buf[s->cur], s->buf[s->cur ^ 1], s->N, s->nu, s->u, s->stream));
-        s->cur ^= 1;
-        s->launches += 1;
+        if (check) CK(drho_change(s->storage, s->buf[s->cur], shifted(s), s->N, prev, maxbits, 0, s->stream));
+        if (s->scheme == KIN_LBE_MRT) {
+            CK(lbe_consistent_step(s->storage, s->buf[s->cur], s->buf[s->cur ^ 1], s->N, s->nu, s->u, s->stream));
+            s->cur ^= 1;
+            s->launches += 1;
+        } else {
+            // a plain DUGKS step, then the momentum back to rho0 u0
+            if (int r = launch_step(s)) return r;
+            CK(dugks_reset_momentum(s->storage, s->buf[s->cur], s->N, s->u, s->stream));
+            s->launches += 1;
+        }
         if (check) {
             CK(cudaMemsetAsync(maxbits, 0, sizeof(unsigned), s->stream));
-            CK(drho_change(s->storage, s->buf[s->cur], true, s->N, prev, maxbits, 1, s->stream));
+            CK(drho_change(s->storage, s->buf[s->cur], shifted(s), s->N, prev, maxbits, 1, s->stream));
             unsigned bits = 0;
             CK(cudaMemcpyAsync(s->h_pin, maxbits, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream));
             CK(cudaStreamSynchronize(s->stream));

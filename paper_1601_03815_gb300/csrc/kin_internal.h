@@ -31,6 +31,11 @@ cudaError_t dugks_step(int storage, const void* src, void* dst, void* fbp, int N
 cudaError_t dugks_step_fused(int storage, const void* src, void* dst, int N, double nu, double dt,
                              int tile_y, int zchunk, cudaStream_t stream, float* uvel = nullptr);
 
+// The momentum reset of a DUGKS consistent-initialisation iteration: f-tilde
+// (in place) gets momentum rho0 u0 (FP64 [3][N^3], device) back along the
+// linear term of the equilibrium.
+cudaError_t dugks_reset_momentum(int storage, void* f, int N, const double* u0, cudaStream_t stream);
+
 // One iteration of the consistent initialisation of an LBE state (pull
 // layout): the step with the momentum held at u0 (FP64 [3][N^3], device).
 cudaError_t lbe_consistent_step(int storage, const void* src, void* dst, int N, double nu, const double* u0,

@@ -53,13 +53,50 @@ def test_converged_density_is_the_taylor_green_pressure(kin):
     sim.close()
 
 
-def test_dugks_and_bad_arguments_are_rejected(kin):
-    sim = kin.Sim(8, kin.DUGKS, NU, 0.1, 0.5)
-    with pytest.raises(kin.KinError) as e:
-        sim.init_consistent(10)
-    assert e.value.code == kin.KIN_EINVAL
+@pytest.mark.parametrize("storage,tol", [(3, 1e-12), (0, 1e-5)])
+@pytest.mark.parametrize("N", [16, 15])
+def test_dugks_iterations_match_the_oracle(kin, orc, storage, tol, N):
+    """DUGKS (Sec. IV.A: "as for the LBE and DUGKS methods"): a plain step
+    and the momentum set back to rho0 u0, 40 iterations against the oracle."""
+    dt = 0.5
+    u = ki.random_velocity(N, N, N, 950 + N, 0.03)
+    sim = kin.Sim(N, kin.DUGKS, NU, 0.1, dt, storage)
+    sim.set_velocity(u)
+    iters, res = sim.init_consistent(40, -1.0)
+    assert iters == 40 and res > 0.0
+    ref, rres = orc.dugks_consistent(u, NU, dt, 40)
+    assert _err(sim.get_f(), ref) < tol
+    assert abs(res / rres[-1] - 1) < 1e-3
+    assert sim.steps_taken == 0
+    sim.step(2)
+    E, eps = sim.stats()
+    assert np.isfinite(E) and E > 0
     sim.close()
-    sim = kin.Sim(8, kin.LBE_MRT, NU, 0.1, 1.0)
-    with pytest.raises(kin.KinError):
-        sim.init_consistent(0)
+
+
+def test_dugks_converged_density_is_the_taylor_green_pressure(kin):
+    N, U = 32, 0.02
+    k = 2 * np.pi / N
+    z, y, x = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    u = np.zeros((3, N, N, N))
+    u[0] = U * np.sin(k * x) * np.cos(k * y)
+    u[1] = -U * np.cos(k * x) * np.sin(k * y)
+    sim = kin.Sim(N, kin.DUGKS, NU, 0.1, 0.5, kin.F64)
+    sim.set_velocity(u)
+    iters, res = sim.init_consistent(6000, 1e-14)
+    assert iters < 6000 and res <= 1e-14
+    f = sim.get_f()
+    d = f.sum(axis=0)
+    exact = 0.75 * U ** 2 * (np.cos(2 * k * x) + np.cos(2 * k * y))
+    assert abs(d.mean()) < 1e-16
+    assert np.abs(d - exact).max() / np.abs(exact).max() < 0.025
     sim.close()
+
+
+def test_bad_arguments_are_rejected(kin):
+    for scheme, dt in ((kin.LBE_MRT, 1.0), (kin.DUGKS, 0.5)):
+        sim = kin.Sim(8, scheme, NU, 0.1, dt)
+        with pytest.raises(kin.KinError) as e:
+            sim.init_consistent(0)
+        assert e.value.code == kin.KIN_EINVAL
+        sim.close()

@@ -58,6 +58,36 @@ def test_ensemble_is_bitwise_equal_to_solo_runs(kin, orc, tuning):
         s.close()
 
 
+def test_ensemble_members_match_the_oracle(kin, orc):
+    """Each member of a mixed ensemble (both schemes, uneven N, ragged tiles,
+    two launches) against the FP64 oracle stepped alone, element by element:
+    max |f_i - f_i^oracle| / max |f_i^oracle| <= 1e-5 per population."""
+    members, states = [], []
+    specs = [("lbe", 8, 0.011), ("dugks", 12, 0.013), ("dugks", 9, 0.02), ("lbe", 13, 0.017),
+             ("dugks", 16, 0.009)]
+    for k, (scheme, N, nu) in enumerate(specs):
+        f0 = _state(orc, N, 900 + k)
+        dt = 1.0 if scheme == "lbe" else 0.45
+        sim = kin.Sim(N, kin.LBE_MRT if scheme == "lbe" else kin.DUGKS, nu, 0.1, dt, kin.F32)
+        sim.set_f(f0)
+        members.append((sim, scheme, nu, dt))
+        states.append(sim.get_f())  # the stored FP32 state the GPU steps from
+    ens = kin.Ensemble([m[0] for m in members])
+    ens.set_tuning(tile_y=4, zchunk=5, lbe_nodes=256)
+    ens.step(2)
+    ens.step(1)
+    for (sim, scheme, nu, dt), f in zip(members, states):
+        ref = f
+        for _ in range(3):
+            ref = orc.step(scheme, ref, nu, dt)
+        got = sim.get_f()
+        scale = np.abs(ref).reshape(19, -1).max(axis=1)
+        err = (np.abs(got - ref).reshape(19, -1).max(axis=1) / scale).max()
+        assert err < 1e-5, (scheme, sim.N, err)
+        sim.close()
+    ens.close()
+
+
 def test_ensemble_barrier_timeout_is_bounded_and_harmless(kin, orc):
     import time
 

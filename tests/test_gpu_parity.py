@@ -258,3 +258,30 @@ def test_errors_and_edge_cases(kin):
     E, eps = sim.stats()  # zero state
     assert E == 0.0 and eps == 0.0
     sim.close()
+
+
+@pytest.mark.parametrize("case", [
+    # DUGKS at CFL 0.9, the stability sweep's time step (Sec. IV.D): dt = 0.9 / sqrt(2)
+    ("dugks", 0.9 / np.sqrt(2.0), 0.013),
+    ("dugks", 0.9 / np.sqrt(2.0), 2e-7),
+    # the sweep's smallest viscosities: tau = 3 nu = 6e-7 for DUGKS (c1 = 1 - c2
+    # ~ 5e-6, b ~ 1.5), s9 -> 2 for MRT-LBE
+    ("dugks", 0.5, 2e-7),
+    ("lbe", 1.0, 5e-5),
+    ("lbe", 1.0, 2e-7),
+])
+@pytest.mark.parametrize("storage", [3, 0])
+@pytest.mark.parametrize("N", [12, 33])
+def test_one_step_parity_sweep_regime(kin, orc, case, storage, N):
+    """One step at the stability sweep's parameters (CFL 0.9 and viscosities
+    down to 2e-7) against the oracle, at the tolerances of the plain regime."""
+    scheme, dt, nu = case
+    f0 = _state(orc, N, 700 + N)
+    sim = kin.Sim(N, _scheme(kin, scheme), nu, 0.1, dt, storage)
+    sim.set_f(f0)
+    f_in = sim.get_f()
+    sim.step(1)
+    got = sim.get_f()
+    ref = orc.step(scheme, f_in, nu, dt)
+    assert _err(got, ref) < TOL[storage]
+    sim.close()
