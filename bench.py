@@ -18,9 +18,11 @@ workload (a smaller box from the same recipe) on the host cores.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -56,6 +58,9 @@ def parse():
     p.add_argument("--no-extras", action="store_true",
                    help="skip the ensemble, serving and reduced-precision reports")
     p.add_argument("--serving-seconds", type=float, default=15.0)
+    p.add_argument("--record-counters", nargs="+", metavar="NCU_CSV",
+                   help="write the counters record from ncu --csv logs of one fused DUGKS launch and exit")
+    p.add_argument("--record-command", default="", help="the ncu command line, for the counters record")
     return p.parse_args()
 
 
@@ -66,6 +71,80 @@ def _peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def _sm_max_mhz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["sm_max_mhz"])
+    except Exception:
+        return 2070.0
+
+
+# The fused DUGKS kernel's translation unit, its headers and the build flags:
+# DRAM traffic and instruction counts recorded from an ncu capture hold only
+# while these are unchanged.
+KERNEL_SOURCES = ("dugks_fused.cu", "dugks_tile.cuh", "dugks_face.cuh", "pair_math.cuh", "kin_common.cuh",
+                  "kin_internal.h")
+COUNTERS_RECORD = "profiles/dugks_fused_kernel_256_f32_counters.md"
+SMS, SCHEDULERS = 152, 4  # GB300: streaming multiprocessors, warp schedulers per SM
+
+
+def kernel_source_hash() -> str:
+    from paper_1601_03815_gb300 import build as b
+
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(b.CSRC, name), "rb") as fh:
+            h.update(name.encode() + b"\0" + fh.read() + b"\0")
+    h.update(" ".join(b.NVCC_FLAGS[:4] + b.ARCH).encode())
+    return h.hexdigest()[:16]
+
+
+def read_counters(path=COUNTERS_RECORD) -> dict:
+    """`key = value` lines of the fenced block of a counters record."""
+    out = {}
+    try:
+        with open(os.path.join(ROOT, path)) as fh:
+            inside = False
+            for line in fh:
+                if line.startswith("```"):
+                    inside = not inside
+                    continue
+                if inside and "=" in line:
+                    k, v = (t.strip() for t in line.split("=", 1))
+                    out[k] = v
+    except OSError:
+        pass
+    return out
+
+
+def record_counters(csv_paths, workload: str, command: str, path=COUNTERS_RECORD) -> None:
+    """Write the counters record from ncu --csv logs of one launch of the fused
+    DUGKS kernel (dram__bytes_read/write.sum, smsp__inst_executed.sum)."""
+    import csv
+
+    vals = {}
+    for p in csv_paths:
+        with open(p) as fh:
+            rows = [r for r in csv.reader(fh) if len(r) > 10]
+        hdr = rows[0]
+        for r in rows[1:]:
+            d = dict(zip(hdr, r))
+            if "dugks_fused" in d.get("Kernel Name", ""):
+                vals[d["Metric Name"]] = int(float(d["Metric Value"].replace(",", "")))
+    lines = ["kernel_sources_sha256 = %s" % kernel_source_hash(),
+             "workload = %s" % workload,
+             "dram_bytes_read = %d" % vals["dram__bytes_read.sum"],
+             "dram_bytes_write = %d" % vals["dram__bytes_write.sum"],
+             "warp_instructions = %d" % vals["smsp__inst_executed.sum"]]
+    with open(os.path.join(ROOT, path), "w") as fh:
+        fh.write("# Counters of one fused DUGKS launch, 256^3 FP32 (read by bench.py)\n\n")
+        fh.write("Command (GB300; each ncu run is one pass, checked on a 128^3 capture of the same metric\n"
+                 "group first; the plain command exited 0 before it):\n\n    %s\n\n" % command)
+        fh.write("bench.py reports `traffic` = read + write and the issue roof from these values\n"
+                 "while the kernel sources hash to the recorded value, and null otherwise.\n\n")
+        fh.write("```\n%s\n```\n" % "\n".join(lines))
 
 
 class ClockSampler:
@@ -155,32 +234,64 @@ def whole_job_mlups(cells_per_rank: int, steps: int, world: int, tmax: float) ->
     return world * cells_per_rank * steps / tmax / 1e6
 
 
-def cpu_baseline_sample(seconds_target: float = 15.0):
-    """Time the FP64 oracle (as it stands) on a 128^3 box of the same recipe:
-    one LBE and one DUGKS step, repeated while under the time budget."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), else what Python reports."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline_sample(steps: int = 1):
+    """The FP64 oracle (as it stands) on the host cores, on the 128^3
+    workloads of the CPU-baseline plan: C2 (k0 = 8, Ma = 0.1, Re_lambda = 25,
+    seed 1200) and the paper-parity P1 (the Sec. IV.C field shape, u' = 0.032,
+    nu = 1.2395e-2 of Table I), `steps` MRT-LBE and `steps` DUGKS (dt = 0.5)
+    steps each, with all host cores and with 16 threads (the paper's 16 MPI
+    cores).  The headline value is C2 with all cores."""
     import kin_inputs as ki
     import oracle
 
     oracle.build()
     n = 128
-    u, info = ki.dhit_velocity(n, 1300, K0, MA, return_info=True)
-    nu = ki.nu_from_re_lambda(info["u_prime"], info["omega"], RE_LAMBDA)
-    f = oracle.equilibrium_field(u)
-    g = f
-    t0 = time.perf_counter()
-    reps = 0
-    while True:
-        g = oracle.lbe_step(f, nu)
-        g = oracle.dugks_step(f, nu, 0.5)
-        reps += 1
-        if time.perf_counter() - t0 > seconds_target / 2 or reps >= 4:
-            break
-    dt = time.perf_counter() - t0
-    del g
-    return {"value": 2 * reps * n ** 3 / dt / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": "%d x (one MRT-LBE + one DUGKS step) on a %d^3 box of the same recipe "
-                      "(k0=8, Ma=0.15), FP64, %.1f s" % (reps, n, dt)}
+    nproc = os.cpu_count() or 1
+    cases = {}
+    u, info = ki.dhit_velocity(n, 1200, 8.0, 0.1, return_info=True)
+    cases["C2"] = (u, ki.nu_from_re_lambda(info["u_prime"], info["omega"], 25.0))
+    u, _ = ki.dhit_velocity(n, 1700, math.sqrt(2.0 / 0.14), 0.032 / math.sqrt(1.0 / 3.0), return_info=True)
+    cases["P1"] = (u, 1.2395e-2)
+    threads = sorted({nproc, 16})
+    runs = {}
+    for name, (u, nu) in cases.items():
+        f = oracle.equilibrium_field(u)
+        for th in threads:
+            oracle.set_num_threads(th)
+            rec = {}
+            for scheme, dt in (("lbe", 1.0), ("dugks", 0.5)):
+                g = oracle.step(scheme, f, nu, dt)  # warm (page-in, thread start)
+                t0 = time.perf_counter()
+                for _ in range(steps):
+                    g = oracle.step(scheme, g, nu, dt)
+                rec[scheme + "_mlups"] = steps * n ** 3 / (time.perf_counter() - t0) / 1e6
+            runs["%s_%dthreads" % (name, th)] = rec
+        del f
+    oracle.set_num_threads(nproc)
+    head = runs["C2_%dthreads" % nproc]
+    # one LBE + one DUGKS step per bench step: cell updates over both times
+    value = 2.0 / (1.0 / head["lbe_mlups"] + 1.0 / head["dugks_mlups"])
+    return {"value": value, "unit": "MLUPS", "cores": nproc, "kind": "oracle", "cpu": cpu_model(),
+            "nproc": nproc,
+            "sample": "FP64 oracle, 128^3: C2 (k0=8, Ma=0.1, Re_lambda=25) and P1 (Sec. IV.C field, "
+                      "u'=0.032, nu=1.2395e-2), %d MRT-LBE + %d DUGKS steps each, at %s threads; value = "
+                      "C2 at all %d cores, one LBE + one DUGKS step per update pair" % (
+                          steps, steps, " and ".join(str(t) for t in threads), nproc),
+            "runs": runs,
+            "paper": {"lbe_mlups": 128 ** 3 / 0.666 / 1e6, "dugks_mlups": 128 ** 3 / 0.911 / 1e6,
+                      "hardware": "16 CPU cores, MPI (Sec. IV.D)"}}
 
 
 def extras(args) -> dict:
@@ -416,12 +527,24 @@ def run_ours(args):
     dom = "dugks" if t_dug >= t_lbe else "lbe"
     t_dom = t_dug if dom == "dugks" else t_lbe
     achieved = bpc * cells / t_dom / 1e9
-    # DRAM read + write bytes of one ncu capture of the current fused DUGKS
-    # kernel on this workload (256^3 FP32, one launch after three warm-up
-    # launches): dram__bytes_read.sum + dram__bytes_write.sum
-    traffic = None
+    # DRAM traffic and warp instructions of one launch of the fused DUGKS
+    # kernel on this workload, from the counters record, while the kernel's
+    # sources are the ones it was captured from
+    traffic, issue, traffic_source = None, None, None
     if dom == "dugks" and args.storage == "f32" and N == 256:
-        traffic = 1496695040 + 1292900608
+        rec = read_counters()
+        if rec and rec.get("kernel_sources_sha256") == kernel_source_hash():
+            traffic = int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
+            traffic_source = "%s (kernel sources sha256 %s)" % (COUNTERS_RECORD, rec["kernel_sources_sha256"])
+            inst = int(rec["warp_instructions"])
+            peak_issue = SMS * SCHEDULERS * _sm_max_mhz() * 1e6
+            issue = {"bound": "issue", "achieved": inst / t_dom, "peak": peak_issue,
+                     "peak_kind": "nominal: %d SMs x %d schedulers x 1 warp instruction per cycle x %.0f MHz"
+                                  % (SMS, SCHEDULERS, _sm_max_mhz()),
+                     "unit": "warp inst/s", "frac": inst / t_dom / peak_issue,
+                     "warp_instructions_per_launch": inst}
+        else:
+            traffic_source = "none: the kernel sources differ from those of %s" % COUNTERS_RECORD
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tmax / args.steps,
@@ -431,8 +554,8 @@ def run_ours(args):
         "per_scheme": per,
         "roofline": {"bound": "hbm", "kernel": "%s step" % dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic,
-                     "algorithmic_bytes_per_launch": bpc * cells},
+                     "traffic": traffic, "traffic_source": traffic_source,
+                     "algorithmic_bytes_per_launch": bpc * cells, "issue": issue},
         "clocks": clocks.summary(),
         "gpu_launches": launches * world,
         "e2e": e2e,
@@ -458,6 +581,10 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.record_counters:
+        record_counters(args.record_counters, "256^3 FP32 fused DUGKS step (bench.py default workload)",
+                        args.record_command)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -50,7 +50,9 @@ enum kin_status {
     KIN_ECUDA = -3,      /* a CUDA / cuFFT call failed */
     KIN_ENONFINITE = -4, /* the state holds NaN/Inf (the run blew up) */
     KIN_ETIMEOUT = -5,   /* a bounded device-side wait gave up */
-    KIN_ESTATE = -6      /* call not valid in the current state */
+    KIN_ESTATE = -6,     /* call not valid in the current state */
+    KIN_EGUARD = -7,     /* a guard region around a state buffer was overwritten */
+    KIN_EDEBUG = -8      /* an index check of the debug build failed */
 };
 
 /* D3Q19 velocity set (Sec. II.A, Eq. 5) in the population order used by every
@@ -180,13 +182,36 @@ int kin_derived_stats(kin_sim* sim, double* out, double* D);
  * synchronise the device) or applications whose device memory is reserved by
  * their own allocator.  It allocates nothing: its scratch, the partial sums of
  * the reduction, is a fixed 19,456-byte array inside the library that every
- * device loading the library keeps until the process exits.  The first call on
- * a device looks up that array's address (cudaGetSymbolAddress) with the
- * device current; make that first call before any stream capture.  All calls
+ * device loading the library keeps until the process exits.  Every call looks
+ * up that array's address in the current device's context
+ * (cudaGetSymbolAddress); the first call on a device also loads the library's
+ * device code there, so make it before any stream capture.  All calls
  * share the array: calls whose work overlaps on the GPU race and must be
  * ordered by the caller (one stream, or events).  N must be in [2, 1024];
  * larger N returns KIN_EINVAL.  nu >= 0.  u and out are the caller's. */
 int kin_energy_dissipation_noalloc(const double* u, int N, double nu, double* out, void* stream);
+
+/* Checks that stand in for a memory checker (no counterpart in the paper).
+ * kin_check_guards: each state buffer sits between two 64 KiB guard regions
+ * filled with the byte 0xA5 at kin_create; after the stream is synchronised
+ * the four regions are read back and compared.  KIN_OK, or KIN_EGUARD naming
+ * the buffer, side and first changed byte (a kernel wrote outside the state).
+ * Synchronous.
+ * kin_debug_status: *is_debug (may be NULL) = 1 when this library was built
+ * with KIN_DEBUG, whose stencil kernels check every global offset and the
+ * shared-memory slot and row indices before use, skip an access that fails
+ * and record the first failure (bits 40..47: check site, bits 0..39: the
+ * offending value) instead of trapping.  *word (may be NULL) receives that
+ * record, 0 if every check passed (always 0 in the release build); reset != 0
+ * clears it.  Returns KIN_EDEBUG if a check failed, else KIN_OK.  Acts on the
+ * current device. */
+int kin_check_guards(kin_sim* sim);
+int kin_debug_status(int* is_debug, unsigned long long* word, int reset);
+
+/* Test hook for kin_check_guards: the host changes one byte of a guard region
+ * (buffer 0 or 1, side 0 = before the data, 1 = after) with cudaMemset.
+ * Synchronous.  KIN_EINVAL for other buffer or side values. */
+int kin_test_corrupt_guard(kin_sim* sim, int buffer, int side);
 
 /* Number of spectrum shells for edge N: 1 + floor(sqrt(3) (N/2) + 1/2). */
 int kin_num_shells(int N);

@@ -30,9 +30,12 @@ KIN_ECUDA = -3
 KIN_ENONFINITE = -4
 KIN_ETIMEOUT = -5
 KIN_ESTATE = -6
+KIN_EGUARD = -7
+KIN_EDEBUG = -8
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libkin.so")
+DEBUG_LIB_PATH = os.path.join(_PKG, "libkin_debug.so")
 _lib = None
 _lock = threading.Lock()
 
@@ -84,6 +87,9 @@ def _declare(lib):
         "kin_last_error": (ctypes.c_char_p, []),
         "kin_destroy": (None, [P]),
         "kin_energy_dissipation_noalloc": (c_int, [P, c_int, c_double, P, P]),
+        "kin_check_guards": (c_int, [P]),
+        "kin_test_corrupt_guard": (c_int, [P, c_int, c_int]),
+        "kin_debug_status": (c_int, [P, P, c_int]),
         "kin_ensemble_create": (c_int, [P, c_int, P]),
         "kin_ensemble_set_tuning": (c_int, [P, c_int, c_int, c_int]),
         "kin_ensemble_step": (c_int, [P, c_int]),
@@ -98,20 +104,31 @@ def _declare(lib):
     return lib
 
 
-def load(build_if_needed: bool = True):
-    """Load libkin.so (building it with nvcc first if it is missing or stale)."""
+def load(build_if_needed: bool = True, debug: bool = False):
+    """Load libkin.so, or with debug the index-checking build libkin_debug.so
+    (building them with nvcc first if missing or stale).  A process loads one
+    of the two: the first call decides."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
         from . import build as _build
 
-        if build_if_needed and not _build.up_to_date():
+        path = DEBUG_LIB_PATH if debug else LIB_PATH
+        if build_if_needed and not _build.up_to_date(path):
             _build.build()
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libkin.so not found at %s; run paper_1601_03815_gb300.build" % LIB_PATH)
-        _lib = _declare(ctypes.CDLL(LIB_PATH, mode=ctypes.RTLD_GLOBAL))
+        if not os.path.exists(path):
+            raise RuntimeError("%s not found; run paper_1601_03815_gb300.build" % path)
+        _lib = _declare(ctypes.CDLL(path, mode=ctypes.RTLD_GLOBAL))
         return _lib
+
+
+def debug_status(reset: bool = False):
+    """kin_debug_status: (is_debug_build, first failed check or 0)."""
+    isd = ctypes.c_int(0)
+    word = ctypes.c_uint64(0)
+    lib().kin_debug_status(ctypes.byref(isd), ctypes.byref(word), int(reset))
+    return bool(isd.value), int(word.value)
 
 
 def lib():
@@ -292,6 +309,16 @@ class Sim:
 
     def sync(self):
         _check(lib().kin_sync(self._h), "kin_sync")
+
+    def check_guards(self):
+        """kin_check_guards: raise KinError (KIN_EGUARD) if a guard region
+        around a state buffer was overwritten."""
+        _check(lib().kin_check_guards(self._h), "kin_check_guards")
+
+    def corrupt_guard(self, buffer: int, side: int):
+        """kin_test_corrupt_guard: change one byte of a guard region from the
+        host, for tests of kin_check_guards."""
+        _check(lib().kin_test_corrupt_guard(self._h, int(buffer), int(side)), "kin_test_corrupt_guard")
 
     @property
     def nu(self) -> float:

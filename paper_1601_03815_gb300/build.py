@@ -1,8 +1,10 @@
 """Build libkin.so in-tree for sm_103a (GB300) with nvcc.
 
 Each .cu file under csrc/ is compiled in parallel, then linked with cuFFT into
-paper_1601_03815_gb300/libkin.so.  Rebuilds only when a source is newer than
-the library.  Usage: ``python -m paper_1601_03815_gb300.build [--force]``.
+paper_1601_03815_gb300/libkin.so, and a second time with -DKIN_DEBUG into
+libkin_debug.so (the stencil kernels check their indices and record the first
+failure instead of trapping; see csrc/kin_debug.cuh).  Rebuilds only what is
+older than its sources.  Usage: ``python -m paper_1601_03815_gb300.build [--force]``.
 """
 from __future__ import annotations
 
@@ -19,6 +21,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libkin.so")
+DEBUG_OBJDIR = os.path.join(PKG, "_build_debug")
+DEBUG_LIB = os.path.join(PKG, "libkin_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
               "-I", INCLUDE, "-I", CSRC] + ARCH
@@ -43,15 +47,15 @@ def _deps():
             + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)])
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(OBJDIR, os.path.basename(src)[:-3] + ".o")
+def _compile(src: str, objdir: str, extra: list[str]) -> str:
+    obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
     cmd = [nvcc(), "-c", src, "-o", obj] + NVCC_FLAGS + extra
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -59,23 +63,37 @@ def _compile(src: str, extra: list[str]) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    """Compile every csrc/*.cu for sm_103a and link libkin.so; returns its path."""
-    if not force and up_to_date():
-        return LIB
-    extra = list(extra or [])
-    os.makedirs(OBJDIR, exist_ok=True)
-    srcs = _sources()
-    with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    tmp = LIB + ".tmp%d" % os.getpid()
+def _link(objs: list[str], lib: str) -> None:
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-lcufft", "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
-    os.replace(tmp, LIB)
-    if verbose:
-        print("built", LIB)
+    os.replace(tmp, lib)
+
+
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, debug: bool = True) -> str:
+    """Compile every csrc/*.cu for sm_103a and link libkin.so (and, with
+    debug, libkin_debug.so), the translation units of both in one parallel
+    pool; returns the path of libkin.so."""
+    extra = list(extra or [])
+    targets = [(LIB, OBJDIR, extra)]
+    if debug:
+        targets.append((DEBUG_LIB, DEBUG_OBJDIR, extra + ["-DKIN_DEBUG"]))
+    targets = [t for t in targets if force or not up_to_date(t[0])]
+    if not targets:
+        return LIB
+    srcs = _sources()
+    jobs = []
+    for lib, objdir, flags in targets:
+        os.makedirs(objdir, exist_ok=True)
+        jobs += [(lib, src, objdir, flags) for src in srcs]
+    with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(lambda j: (j[0], _compile(j[1], j[2], j[3])), jobs))
+    for lib, _, _ in targets:
+        _link([o for l, o in objs if l == lib], lib)
+        if verbose:
+            print("built", lib)
     return LIB
 
 

@@ -58,6 +58,8 @@ static cudaError_t launch_fused(const void* src, void* dst, int N, double nu, do
     }
 }
 
+KIN_DEBUG_ACCESSOR(debug_word_dugks)
+
 cudaError_t dugks_step_fused(int storage, const void* src, void* dst, int N, double nu, double dt,
                              int ty, int zchunk, cudaStream_t stream, float* uvel) {
     switch (storage) {

@@ -35,6 +35,7 @@
 
 #include "dugks_face.cuh"
 #include "kin_common.cuh"
+#include "kin_debug.cuh"
 #include "pair_math.cuh"
 
 namespace kin {
@@ -353,19 +354,25 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
         if constexpr (kStage16<S>) {
             if (use16) {
                 if (lane <= 16) {
-                    const S* p = src + (size_t)zwrap(z) * nn + rowidx;
+                    const size_t o = (size_t)zwrap(z) * nn + rowidx;
                     const int s = rslot_of(z);
 #pragma unroll
-                    for (int i = 0; i < Q; ++i) cp_async4(&stage16->raw[s][i][row][2 * lane], p + i * plane);
+                    for (int i = 0; i < Q; ++i)
+                        if (KIN_CHECK(o + i * plane + 1 < Q * plane, DBG_DUGKS_LOAD, o + i * plane + 1) &&
+                            KIN_CHECK(s >= 0 && s < 4, DBG_DUGKS_SLOT, s))
+                            cp_async4(&stage16->raw[s][i][row][2 * lane], src + o + i * plane);
                 }
                 cp_async_commit();
             }
         }
         if constexpr (kAsyncStage<S>) {
-            const S* p = src + (size_t)zwrap(z) * nn + colidx;
+            const size_t o = (size_t)zwrap(z) * nn + colidx;
             const int s = rslot_of(z);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) cp_async4(&stage->raw[s][i][row][lane], p + i * plane);
+            for (int i = 0; i < Q; ++i)
+                if (KIN_CHECK(o + i * plane < Q * plane, DBG_DUGKS_LOAD, o + i * plane) &&
+                    KIN_CHECK(s >= 0 && s < 4, DBG_DUGKS_SLOT, s))
+                    cp_async4(&stage->raw[s][i][row][lane], src + o + i * plane);
             cp_async_commit();
         }
     };
@@ -381,8 +388,10 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
                                to_float(stage16->raw[s][2 * q + 2][row][lane + 1]));
                 }
             }
-            const S* p = src + (size_t)zwrap(z) * nn + colidx;
-            return pmk(Traits<S>::load(p + (2 * q + 1) * plane), Traits<S>::load(p + (2 * q + 2) * plane));
+            const size_t o = (size_t)zwrap(z) * nn + colidx;
+            if (!KIN_CHECK(o + (2 * q + 2) * plane < Q * plane, DBG_DUGKS_LOAD, o + (2 * q + 2) * plane))
+                return pmk(C(0), C(0));
+            return pmk(Traits<S>::load(src + o + (2 * q + 1) * plane), Traits<S>::load(src + o + (2 * q + 2) * plane));
         }
     };
     auto raw_rest = [&](int z) -> C {
@@ -392,7 +401,9 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
             if constexpr (kStage16<S>) {
                 if (use16) return to_float(stage16->raw[rslot_of(z)][0][row][lane + 1]);
             }
-            return Traits<S>::load(src + (size_t)zwrap(z) * nn + colidx);
+            const size_t o = (size_t)zwrap(z) * nn + colidx;
+            if (!KIN_CHECK(o < plane, DBG_DUGKS_LOAD, o)) return C(0);
+            return Traits<S>::load(src + o);
         }
     };
 
@@ -442,7 +453,8 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
                     if constexpr (T == 0) {
                         v.G[0][K] = psub(sm.ring[s0][p][row][lp], sm.ring[s0][p][row][lm]);
                     } else if constexpr (T == 1) {
-                        v.G[1][K] = psub(sm.ring[s0][p][row + 1][lane], sm.ring[s0][p][row - 1][lane]);
+                        if (KIN_CHECK(row >= 1 && row <= TY, DBG_DUGKS_ROW, row))
+                            v.G[1][K] = psub(sm.ring[s0][p][row + 1][lane], sm.ring[s0][p][row - 1][lane]);
                     } else {
                         v.G[2][K] = psub(sm.ring[sp1][p][row][lane], sm.ring[sm1][p][row][lane]);
                     }
@@ -487,6 +499,9 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
 
     for (int z = z0; z <= zend; ++z) {
         const bool last = z == zend;
+        if (!KIN_CHECK(s_m1 >= 0 && s_m1 < 3 && s_0 >= 0 && s_0 < 3 && s_p1 >= 0 && s_p1 < 3, DBG_DUGKS_SLOT,
+                       s_m1 * 100 + s_0 * 10 + s_p1))
+            break;
         if (!last) {
             if constexpr (kAsyncStage<S> || kStage16<S>) wait_copies();
             prestep(z + 1, s_p1);
@@ -574,7 +589,8 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
                     Dprev[p] = sg > 0 ? dy : pneg(dy);
                 }
             });
-            if (valid) {
+            if (valid && KIN_CHECK((size_t)(z - 1) * nn + colidx < plane, DBG_DUGKS_STORE,
+                                   (size_t)(z - 1) * nn + colidx)) {
                 const size_t c = (size_t)(z - 1) * nn + colidx;
                 [[maybe_unused]] C uv[3] = {C(0), C(0), C(0)};
                 // velocity sums in population order: the same additions as the

@@ -23,6 +23,8 @@
 #include "kin_sim.h"
 #include "lbe_node.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <cstddef>
 #include <map>
@@ -80,7 +82,7 @@ __global__ void __launch_bounds__(32 * (TY + 2), 1)
                 int abort = ld_relaxed(status) != 0;
                 // stall_test raises the target of step 1 beyond reach, to
                 // exercise the bounded wait
-                const unsigned target = (unsigned)(s * M.ntiles) + (stall_test && s == 1 ? 1u : 0u);
+                const unsigned target = (unsigned)s * (unsigned)M.ntiles + (stall_test && s == 1 ? 1u : 0u);
                 if (!abort && s > 0) {
                     const long long t0 = clock64();
                     while (ld_acquire(&done[item.x]) < target) {
@@ -136,6 +138,8 @@ __global__ void __launch_bounds__(32 * (TY + 2), 1)
         }
     }
 }
+
+KIN_DEBUG_ACCESSOR(debug_word_ensemble)
 
 }  // namespace kin
 
@@ -317,7 +321,12 @@ int run(kin_ensemble* e, int nsteps, int stall_test) {
     ECK(cudaMemcpyAsync(&status, e->d_status, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
     ECK(cudaStreamSynchronize(e->stream));
     e->launches += 1;
-    if (status != 0) return set_error(KIN_ETIMEOUT, "ensemble member barrier timed out");
+    if (status != 0) {
+        // items of several steps may have run: no member's state is known to
+        // be a whole step, so every member refuses work until it is set again
+        for (kin_sim* s : e->members) s->invalid = true;
+        return set_error(KIN_ETIMEOUT, "ensemble member barrier timed out; the members' states are undefined");
+    }
     for (kin_sim* s : e->members) {
         s->cur ^= (nsteps & 1);
         s->step += nsteps;
@@ -387,11 +396,24 @@ int kin_ensemble_step(kin_ensemble* e, int nsteps) {
     if (!e) return set_error(KIN_EINVAL, "NULL ensemble");
     if (nsteps < 0) return set_error(KIN_EINVAL, "negative step count");
     if (nsteps == 0) return KIN_OK;
+    for (const kin_sim* s : e->members)
+        if (s->invalid) return set_error(KIN_ESTATE, "a member's state is undefined (set it again first)");
+    nvtxRangePushA("kin_ensemble_step");
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(e->device);
-    const int r = run(e, nsteps, 0);
+    // the kernel numbers (step, item) pairs and member progress in 32 bits:
+    // split the steps into launches of at most max_steps
+    const unsigned long long max_steps =
+        std::max<unsigned long long>(1, (0xffffffffull - (unsigned long long)e->grid) / std::max(e->nitems, 1));
+    int r = KIN_OK;
+    for (long long left = nsteps; left > 0 && r == KIN_OK;) {
+        const int n = (int)std::min<unsigned long long>((unsigned long long)left, max_steps);
+        r = run(e, n, 0);
+        left -= n;
+    }
     cudaSetDevice(prev);
+    nvtxRangePop();
     return r;
 }
 

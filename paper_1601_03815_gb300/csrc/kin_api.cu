@@ -6,6 +6,7 @@
 #include "kin_sim.h"
 
 #include <cufft.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -68,6 +69,19 @@ struct DeviceGuard {
     }
 };
 
+// Guard regions before and after each state buffer, filled with kGuardByte
+// at creation: a kernel that writes outside the state shows up in
+// kin_check_guards.
+constexpr size_t kGuardBytes = 64 * 1024;
+constexpr unsigned char kGuardByte = 0xA5;
+
+// NVTX range over one API call (visible in Nsight timelines; a no-op without a
+// tool attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 size_t ncell(const kin_sim* s) { return (size_t)s->N * s->N * s->N; }
 bool shifted(const kin_sim* s) { return s->scheme == KIN_LBE_MRT; }
 size_t state_bytes(const kin_sim* s) { return Q * ncell(s) * storage_bytes(s->storage); }
@@ -96,6 +110,15 @@ size_t nmode(const kin_sim* s) { return (size_t)s->N * s->N * (s->N / 2 + 1); }
 
 int valid(const kin_sim* s) {
     if (!s) return fail(KIN_EINVAL, "NULL simulation handle");
+    return KIN_OK;
+}
+
+// valid() and a defined state (not left part-way by a timed-out ensemble launch)
+int usable(const kin_sim* s) {
+    if (int r = valid(s)) return r;
+    if (s->invalid)
+        return fail(KIN_ESTATE, "the state is undefined after an ensemble launch gave up a wait; set it again "
+                                "with kin_set_f, kin_set_velocity or kin_init_field");
     return KIN_OK;
 }
 
@@ -276,12 +299,16 @@ int kin_create(int N, int scheme, double nu, double Ma, double dt, int storage, 
     }
     const size_t sb = state_bytes(s);
     for (int k = 0; k < 2; ++k) {
-        cudaError_t e = cudaMalloc(&s->buf[k], sb);
+        cudaError_t e = cudaMalloc(&s->base[k], sb + 2 * kGuardBytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return bail(fail(KIN_ENOMEM, "state buffer of %zu bytes: %s", sb, cudaGetErrorString(e)));
         }
-        e = cudaMemsetAsync(s->buf[k], 0, sb, s->stream);
+        s->buf[k] = static_cast<unsigned char*>(s->base[k]) + kGuardBytes;
+        e = cudaMemsetAsync(s->base[k], kGuardByte, kGuardBytes, s->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->buf[k], 0, sb, s->stream);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(static_cast<unsigned char*>(s->buf[k]) + sb, kGuardByte, kGuardBytes, s->stream);
         if (e != cudaSuccess) return bail(fail(KIN_ECUDA, "memset: %s", cudaGetErrorString(e)));
     }
     {
@@ -303,7 +330,7 @@ void kin_destroy(kin_sim* s) {
     DeviceGuard g(s->device);
     if (s->stream) cudaStreamSynchronize(s->stream);
     for (int k = 0; k < 2; ++k)
-        if (s->buf[k]) cudaFree(s->buf[k]);
+        if (s->base[k]) cudaFree(s->base[k]);
     if (s->fbp) cudaFree(s->fbp);
     if (s->u) cudaFree(s->u);
     if (s->u32) cudaFree(s->u32);
@@ -329,10 +356,12 @@ int kin_set_velocity(kin_sim* s, const double* u) {
     CK(cudaStreamSynchronize(s->stream));
     s->step = 0;
     s->epoch += 1;
+    s->invalid = false;
     return KIN_OK;
 }
 
 int kin_init_field(kin_sim* s, uint64_t seed, double k0, double re_lambda) {
+    NvtxRange nvtx_("kin_init_field");
     if (int r = valid(s)) return r;
     if (s->N < 4 || (s->N & 1)) return fail(KIN_EINVAL, "kin_init_field needs even N >= 4, got %d", s->N);
     if (!(k0 > 0.0) || !std::isfinite(k0)) return fail(KIN_EINVAL, "k0 must be positive");
@@ -393,6 +422,7 @@ int kin_init_field(kin_sim* s, uint64_t seed, double k0, double re_lambda) {
     }
     s->step = 0;
     s->epoch += 1;
+    s->invalid = false;
     return KIN_OK;
 }
 
@@ -409,6 +439,7 @@ int kin_set_f(kin_sim* s, const double* f) {
     CK(cudaStreamSynchronize(s->stream));
     s->step = 0;
     s->epoch += 1;
+    s->invalid = false;
     return KIN_OK;
 }
 
@@ -467,7 +498,8 @@ int kin_get_velocity(kin_sim* s, double* u) {
 }
 
 int kin_step(kin_sim* s, int n) {
-    if (int r = valid(s)) return r;
+    NvtxRange nvtx_("kin_step");
+    if (int r = usable(s)) return r;
     if (n < 0) return fail(KIN_EINVAL, "negative step count");
     DeviceGuard g(s->device);
     for (int k = 0; k < n; ++k)
@@ -476,7 +508,8 @@ int kin_step(kin_sim* s, int n) {
 }
 
 int kin_step_stats(kin_sim* s, int n, double* E, double* eps, double* Ek) {
-    if (int r = valid(s)) return r;
+    NvtxRange nvtx_("kin_step_stats");
+    if (int r = usable(s)) return r;
     if (n < 0) return fail(KIN_EINVAL, "negative step count");
     DeviceGuard g(s->device);
     const bool fuse = n > 0 && fused_velocity_ok(s);
@@ -487,7 +520,8 @@ int kin_step_stats(kin_sim* s, int n, double* E, double* eps, double* Ek) {
 }
 
 int kin_init_consistent(kin_sim* s, int max_iter, double tol, int* iters, double* residual) {
-    if (int r = valid(s)) return r;
+    NvtxRange nvtx_("kin_init_consistent");
+    if (int r = usable(s)) return r;
     if (max_iter < 1) return fail(KIN_EINVAL, "max_iter must be >= 1, got %d", max_iter);
     DeviceGuard g(s->device);
     if (int r = ensure_u(s)) return r;
@@ -538,7 +572,8 @@ int kin_init_consistent(kin_sim* s, int max_iter, double tol, int* iters, double
 }
 
 int kin_stats(kin_sim* s, double* E, double* eps, double* Ek) {
-    if (int r = valid(s)) return r;
+    NvtxRange nvtx_("kin_stats");
+    if (int r = usable(s)) return r;
     DeviceGuard g(s->device);
     if (int r = ensure_u(s)) return r;
     if (s->storage == ST_F64) {
@@ -611,7 +646,8 @@ int kin_stats(kin_sim* s, double* E, double* eps, double* Ek) {
 }
 
 int kin_derived_stats(kin_sim* s, double* out, double* D) {
-    if (int r = valid(s)) return r;
+    NvtxRange nvtx_("kin_derived_stats");
+    if (int r = usable(s)) return r;
     if (!out) return fail(KIN_EINVAL, "NULL output");
     DeviceGuard g(s->device);
     if (int r = ensure_u(s)) return r;
@@ -723,10 +759,60 @@ const char* kin_strerror(int code) {
         case KIN_ENONFINITE: return "non-finite state";
         case KIN_ETIMEOUT: return "device wait timed out";
         case KIN_ESTATE: return "invalid state";
+        case KIN_EGUARD: return "a guard region of a state buffer was overwritten";
+        case KIN_EDEBUG: return "an index check of the debug build failed";
     }
     return "unknown status";
 }
 
 const char* kin_last_error(void) { return g_err; }
+
+int kin_check_guards(kin_sim* s) {
+    if (int r = valid(s)) return r;
+    DeviceGuard g(s->device);
+    CK(cudaStreamSynchronize(s->stream));
+    std::vector<unsigned char> h(kGuardBytes);
+    const size_t sb = state_bytes(s);
+    for (int k = 0; k < 2; ++k)
+        for (int side = 0; side < 2; ++side) {
+            const unsigned char* p =
+                side == 0 ? static_cast<const unsigned char*>(s->base[k]) : static_cast<const unsigned char*>(s->buf[k]) + sb;
+            CK(cudaMemcpy(h.data(), p, kGuardBytes, cudaMemcpyDeviceToHost));
+            for (size_t b = 0; b < kGuardBytes; ++b)
+                if (h[b] != kGuardByte)
+                    return fail(KIN_EGUARD, "state buffer %d: guard %s the data overwritten at byte %zu", k,
+                                side == 0 ? "before" : "after", b);
+        }
+    return KIN_OK;
+}
+
+int kin_test_corrupt_guard(kin_sim* s, int buffer, int side) {
+    if (int r = valid(s)) return r;
+    if (buffer < 0 || buffer > 1 || side < 0 || side > 1) return fail(KIN_EINVAL, "buffer and side are 0 or 1");
+    DeviceGuard g(s->device);
+    CK(cudaStreamSynchronize(s->stream));
+    unsigned char* p = side == 0 ? static_cast<unsigned char*>(s->base[buffer]) + kGuardBytes / 2
+                                 : static_cast<unsigned char*>(s->buf[buffer]) + state_bytes(s) + 7;
+    CK(cudaMemset(p, kGuardByte ^ 0xFF, 1));
+    return KIN_OK;
+}
+
+int kin_debug_status(int* is_debug, unsigned long long* word, int reset) {
+#ifdef KIN_DEBUG
+    if (is_debug) *is_debug = 1;
+#else
+    if (is_debug) *is_debug = 0;
+#endif
+    unsigned long long w[3] = {0, 0, 0};
+    CK(debug_word_dugks(&w[0], reset != 0));
+    CK(debug_word_lbe(&w[1], reset != 0));
+    CK(debug_word_ensemble(&w[2], reset != 0));
+    const unsigned long long first = w[0] ? w[0] : (w[1] ? w[1] : w[2]);
+    if (word) *word = first;
+    if (first)
+        return fail(KIN_EDEBUG, "index check failed at site %llu with value %llu", first >> 40,
+                    first & ((1ull << 40) - 1));
+    return KIN_OK;
+}
 
 }  // extern "C"

@@ -53,7 +53,8 @@ cudaError_t velocity_field(int storage, const void* state, bool shifted, int N, 
                            cudaStream_t stream);
 
 // E and eps sums: partials[2 * nblocks] then out[2] = {E, eps} (FP64, fixed
-// order).  nblocks = stats_blocks(N).
+// order).  nblocks = stats_blocks(N) <= kStatsMaxBlocks (8 per SM on 152 SMs).
+constexpr int kStatsMaxBlocks = 1216;
 int stats_blocks(int N);
 // FP32 statistics path for storage types computed in FP32 (F32, F16, BF16).
 cudaError_t velocity_field32(int storage, const void* state, bool shifted, int N, float* u,
@@ -92,6 +93,13 @@ cudaError_t get_population(int storage, int i, const void* state, bool shifted, 
 // out[n][19] canonical f at cells[n].
 cudaError_t sample_cells(int storage, const void* state, bool shifted, int N,
                          const int64_t* cells, int64_t n, double* out, cudaStream_t stream);
+
+// First failed index check of a KIN_DEBUG build in the translation units of
+// the fused DUGKS step, the LBE step and the ensemble kernel (0: none, or not
+// a debug build); reset clears it.
+cudaError_t debug_word_dugks(unsigned long long* word, bool reset);
+cudaError_t debug_word_lbe(unsigned long long* word, bool reset);
+cudaError_t debug_word_ensemble(unsigned long long* word, bool reset);
 
 // Non-finite check of a double array: flag[0] |= 1 if any element is NaN/Inf.
 cudaError_t scan_nonfinite(const double* v, size_t n, int* flag, cudaStream_t stream);

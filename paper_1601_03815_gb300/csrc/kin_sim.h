@@ -13,9 +13,13 @@ struct kin_sim {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     void* buf[2] = {nullptr, nullptr};
+    void* base[2] = {nullptr, nullptr};  // allocations: guard region, buf[k], guard region
     int cur = 0;
     void* fbp = nullptr;  // DUGKS f-bar-plus scratch
     int64_t step = 0;
+    // set when an ensemble launch gave up a bounded wait part-way: the state
+    // is undefined until kin_set_f, kin_set_velocity or kin_init_field
+    bool invalid = false;
     // statistics scratch (lazy)
     double* u = nullptr;      // 3 N^3
     float* u32 = nullptr;     // 3 N^3, the E / eps path of FP32-computed storage

@@ -96,8 +96,10 @@ __global__ void __launch_bounds__(256) lbe_stepv_kernel(const S* __restrict__ sr
         constexpr int I = decltype(ic)::value;
         // row of the source cells x - xi_i (N <= 1024: row offsets fit in 32 bits)
         const S* row = src + (size_t)I * plane + (yo[1 - cy(I)] + zo[1 - cz(I)]);
-        float own[V];
-        vload<S, V>(row + x, own);
+        float own[V] = {};
+        if (KIN_CHECK((size_t)(yo[1 - cy(I)] + zo[1 - cz(I)]) + x + V <= plane && xm < N && xp < N, DBG_LBE_LOAD,
+                      yo[1 - cy(I)] + zo[1 - cz(I)] + x))
+            vload<S, V>(row + x, own);
         if constexpr (cx(I) == 0) {
 #pragma unroll
             for (int k = 0; k < V; ++k) f[k][I] = own[k];
@@ -117,6 +119,7 @@ __global__ void __launch_bounds__(256) lbe_stepv_kernel(const S* __restrict__ sr
         mrt_collide(f[k], rates, drho, jx, jy, jz);
     }
     const int c = x + N * (y + N * z);
+    if (!KIN_CHECK((size_t)c + V <= plane, DBG_LBE_STORE, c)) return;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         float v[V];
@@ -195,6 +198,8 @@ cudaError_t lbe_consistent_step(int storage, const void* src, void* dst, int N, 
     }
     return cudaErrorInvalidValue;
 }
+
+KIN_DEBUG_ACCESSOR(debug_word_lbe)
 
 cudaError_t lbe_step(int storage, const void* src, void* dst, int N, double nu, int block_x,
                      cudaStream_t stream) {

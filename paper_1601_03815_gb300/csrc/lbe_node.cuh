@@ -8,6 +8,7 @@
 #pragma once
 
 #include "kin_common.cuh"
+#include "kin_debug.cuh"
 
 namespace kin {
 
@@ -38,7 +39,8 @@ __device__ __forceinline__ void lbe_gather(const S* __restrict__ src, int N, siz
     static_for<0, Q>([&](auto ic) {
         constexpr int I = decltype(ic)::value;
         const int idx = xo[1 - cx(I)] + yo[1 - cy(I)] + zo[1 - cz(I)];
-        if constexpr (COHERENT) f[I] = (C)src[(size_t)I * plane + idx];
+        if (!KIN_CHECK(idx >= 0 && (size_t)idx < plane, DBG_LBE_LOAD, idx)) f[I] = C(0);
+        else if constexpr (COHERENT) f[I] = (C)src[(size_t)I * plane + idx];
         else f[I] = Traits<S>::load(src + (size_t)I * plane + idx);
     });
 }
@@ -47,6 +49,7 @@ template <typename S>
 __device__ __forceinline__ void lbe_scatter(S* __restrict__ dst, int N, size_t plane, int x, int y, int z,
                                             const typename Traits<S>::C (&f)[Q]) {
     const int c = x + N * (y + N * z);  // N <= 1024
+    if (!KIN_CHECK(c >= 0 && (size_t)c < plane, DBG_LBE_STORE, c)) return;
 #pragma unroll
     for (int i = 0; i < Q; ++i) Traits<S>::store(dst + (size_t)i * plane + c, f[i]);
 }

@@ -102,7 +102,7 @@ constexpr int RED_THREADS = 256;
 int stats_blocks(int N) {
     long long n = (long long)N * N * N;
     long long b = (n + RED_THREADS * 8 - 1) / (RED_THREADS * 8);
-    if (b > 1216) b = 1216;  // 8 per SM on 152 SMs
+    if (b > kStatsMaxBlocks) b = kStatsMaxBlocks;
     if (b < 1) b = 1;
     return (int)b;
 }
@@ -769,36 +769,25 @@ cudaError_t drho_change(int storage, const void* state, bool shifted, int N, dou
 // allocator (a framework's caching allocator, a fixed arena).  For them the
 // per-block partial sums of the reduction live in this fixed array compiled
 // into the library instead of in memory allocated per simulation.  It holds
-// 2 x 1216 doubles (19,456 bytes) and exists on every device that loads the
+// 2 x kStatsMaxBlocks doubles (19,456 bytes) and exists on every device that loads the
 // library until the process exits.  Every call shares it and overwrites the
 // partials it uses before reading them (nothing has to start at zero); calls
 // whose kernels overlap on the GPU race on it.
 namespace {
 
-constexpr int kNoallocMaxBlocks = 1216;
+constexpr int kNoallocMaxBlocks = kin::kStatsMaxBlocks;
 constexpr int kNoallocMaxN = 1024;
-static_assert(kNoallocMaxBlocks >= 1216, "partials must cover stats_blocks() for every N");
+static_assert(kNoallocMaxBlocks >= kin::kStatsMaxBlocks, "partials must cover stats_blocks() for every N");
 
 static __device__ __align__(256) double g_noalloc_partials[2 * kNoallocMaxBlocks];
 
-std::mutex g_noalloc_mu;
-double* g_noalloc_ptr[128] = {};  // device address of the array, per device ordinal
-
-// Device address of the array on `dev` (the current device), looked up once.
-double* noalloc_scratch(int dev, cudaError_t* err) {
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (dev < 0 || dev >= 128) {
-        *err = cudaErrorInvalidDevice;
-        return nullptr;
-    }
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        *err = cudaGetSymbolAddress(&p, g_noalloc_partials);
-        if (*err != cudaSuccess) return nullptr;
-        g_noalloc_ptr[dev] = (double*)p;
-    }
-    *err = cudaSuccess;
-    return g_noalloc_ptr[dev];
+// Device address of the array in the current device's context.  Looked up on
+// every call, not cached: after a context reset the module is loaded again and
+// the array may sit elsewhere.
+double* noalloc_scratch(cudaError_t* err) {
+    void* p = nullptr;
+    *err = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    return *err == cudaSuccess ? (double*)p : nullptr;
 }
 
 }  // namespace
@@ -816,10 +805,8 @@ extern "C" int kin_energy_dissipation_noalloc(const double* u, int N, double nu,
     if (nb > kNoallocMaxBlocks)
         return set_error(KIN_EINVAL, "reduction needs %d blocks, fixed scratch holds %d", nb,
                          kNoallocMaxBlocks);
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return set_error(KIN_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-    double* partials = noalloc_scratch(dev, &e);
+    cudaError_t e;
+    double* partials = noalloc_scratch(&e);
     if (!partials) return set_error(KIN_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
     e = energy_dissipation(u, N, nu, partials, out, (cudaStream_t)stream);
     if (e != cudaSuccess) return set_error(KIN_ECUDA, "reduction launch: %s", cudaGetErrorString(e));

@@ -84,3 +84,14 @@ def test_invalid_arguments_are_rejected_without_a_device(libkin):
     assert libkin.kin_step_stats(None, 1, ctypes.byref(d), ctypes.byref(d), None) == -1
     assert libkin.kin_init_consistent(None, 10, ctypes.c_double(0.0), None, None) == -1
     libkin.kin_destroy(None)  # NULL-safe
+
+
+def test_debug_library_exports_every_declared_symbol():
+    """The KIN_DEBUG build (index checks in the stencil kernels) offers the
+    same boundary."""
+    import paper_1601_03815_gb300.build as b
+
+    b.build()
+    lib = ctypes.CDLL(b.DEBUG_LIB, mode=ctypes.RTLD_LOCAL)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing

@@ -100,8 +100,18 @@ def test_ensemble_barrier_timeout_is_bounded_and_harmless(kin, orc):
     assert time.time() - t0 < 30.0
     for m, f in zip(members, before):
         assert m.steps_taken == 0
+        # the stall was at step 1 of 2, so the state is in fact untouched ...
         np.testing.assert_array_equal(m.get_f(), f)
-    # the ensemble still works afterwards
+        # ... but a timed-out launch leaves every member refusing work until set
+        with pytest.raises(kin.KinError) as e:
+            m.step(1)
+        assert e.value.code == kin.KIN_ESTATE
+    with pytest.raises(kin.KinError) as e:
+        ens.step(1)
+    assert e.value.code == kin.KIN_ESTATE
+    for m, f in zip(members, before):
+        m.set_f(f)
+    # the ensemble works again afterwards
     ens.step(2)
     for s in solo:
         s.step(2)

@@ -43,6 +43,28 @@ def test_noalloc_energy_dissipation_matches_kin_stats(kin):
     sim.close()
 
 
+def test_noalloc_fills_every_partial_slot_against_the_oracle(kin, orc):
+    """N = 144 needs more blocks than the fixed array holds partials for, so
+    the reduction runs with every one of its slots; E and eps against the FP64
+    oracle's definitions of the same field, on two calls in a row."""
+    import numpy as np
+    import torch
+
+    import kin_inputs as ki
+
+    N, nu = 144, 0.015
+    u_h = ki.dhit_velocity(N, 21, 8.0, 0.1)
+    E_o, eps_o = orc.energy_dissipation(u_h, nu)
+    u = torch.from_numpy(np.ascontiguousarray(u_h)).cuda()
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        out.fill_(-1.0)
+        kin.energy_dissipation_noalloc(u.data_ptr(), N, nu, out.data_ptr(), torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        E, eps = out.tolist()
+        assert abs(E / E_o - 1) < 1e-12 and abs(eps / eps_o - 1) < 1e-12, (E, E_o, eps, eps_o)
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(kin):
     lib = kin.lib()
     rc = lib.kin_energy_dissipation_noalloc(ctypes.c_void_p(16), 2048, 0.01, ctypes.c_void_p(16), None)
