@@ -6,7 +6,10 @@
 // every thread runs the cell pre-step (Eq. 19) of its own column for the next
 // plane into a three-plane ring of f-bar-plus in shared memory, fed by
 // cp.async copies of f-tilde issued two planes ahead.  Two block barriers per
-// plane: after the pre-step, and before the y faces.
+// plane: one before the plane's work, whose first part is the pre-step of the
+// next plane (only this thread reads the slot it fills until the next
+// barrier, so its arithmetic interleaves with the faces of this plane), and
+// one before the y faces.
 //
 // Interface reconstruction splits exactly between the two cells of a face.
 // With G_i^t(X) = fbp_i(X + e_t) - fbp_i(X - e_t) the Eq. 13/15/16 value at the
@@ -502,14 +505,12 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
         if (!KIN_CHECK(s_m1 >= 0 && s_m1 < 3 && s_0 >= 0 && s_0 < 3 && s_p1 >= 0 && s_p1 < 3, DBG_DUGKS_SLOT,
                        s_m1 * 100 + s_0 * 10 + s_p1))
             break;
+        __syncthreads();  // fy of plane z - 1 complete; my of plane z - 1 consumed
+        Rec<C> Py;
         if (!last) {
             if constexpr (kAsyncStage<S> || kStage16<S>) wait_copies();
             prestep(z + 1, s_p1);
             if (z + 2 <= zend) issue_plane(z + 2);
-        }
-        __syncthreads();  // ring slot of z + 1 complete; fy of plane z - 1 complete
-        Rec<C> Py;
-        if (!last) {
             CellView<C> v;
             // warp-uniform: rows 1..TY take every difference, the halo rows
             // only those their y records need
