@@ -7,16 +7,18 @@
 namespace kin {
 
 // VEL: also write the velocity of the new state to uvel (FP32-computed storage).
-template <typename S, int TY, bool VEL>
+// EVEN = false: odd N with 2-byte storage, whose tile reads f-tilde from global
+// memory directly instead of staging it.
+template <typename S, int TY, bool VEL, bool EVEN>
 __global__ void __launch_bounds__(32 * (TY + 2), 1)
     dugks_fused_kernel(const S* __restrict__ src, S* __restrict__ dst, int N, int zchunk,
                        DugksCoef<typename Traits<S>::C> kc, float* __restrict__ uvel) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    dugks_tile<S, TY, VEL>(src, dst, N, blockIdx.x, blockIdx.y, blockIdx.z, zchunk, kc, smem_raw, uvel);
+    dugks_tile<S, TY, VEL, EVEN>(src, dst, N, blockIdx.x, blockIdx.y, blockIdx.z, zchunk, kc, smem_raw, uvel);
 }
 
-template <typename S, int TY, bool VEL>
-static cudaError_t launch_fused_t(const void* src, void* dst, int N, int zchunk,
+template <typename S, int TY, bool VEL, bool EVEN>
+static cudaError_t launch_fused_e(const void* src, void* dst, int N, int zchunk,
                                   const DugksCoef<typename Traits<S>::C>& k, float* uvel, cudaStream_t stream) {
     const size_t smem = fused_smem_bytes<S, TY>();
     // the shared-memory limit is a per-device attribute of the kernel: set it
@@ -27,7 +29,7 @@ static cudaError_t launch_fused_t(const void* src, void* dst, int N, int zchunk,
     if (e != cudaSuccess) return e;
     const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
     if (!bit || !(configured.load() & bit)) {
-        e = cudaFuncSetAttribute(dugks_fused_kernel<S, TY, VEL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(dugks_fused_kernel<S, TY, VEL, EVEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
         configured.fetch_or(bit);
@@ -36,8 +38,17 @@ static cudaError_t launch_fused_t(const void* src, void* dst, int N, int zchunk,
     if (zchunk > N) zchunk = N;
     dim3 block(32, TY + 2);
     dim3 grid((N + 29) / 30, (N + TY - 1) / TY, (N + zchunk - 1) / zchunk);
-    dugks_fused_kernel<S, TY, VEL><<<grid, block, smem, stream>>>((const S*)src, (S*)dst, N, zchunk, k, uvel);
+    dugks_fused_kernel<S, TY, VEL, EVEN><<<grid, block, smem, stream>>>((const S*)src, (S*)dst, N, zchunk, k, uvel);
     return cudaGetLastError();
+}
+
+template <typename S, int TY, bool VEL>
+static cudaError_t launch_fused_t(const void* src, void* dst, int N, int zchunk,
+                                  const DugksCoef<typename Traits<S>::C>& k, float* uvel, cudaStream_t stream) {
+    if constexpr (sizeof(S) == 2) {
+        if (N % 2) return launch_fused_e<S, TY, VEL, false>(src, dst, N, zchunk, k, uvel, stream);
+    }
+    return launch_fused_e<S, TY, VEL, true>(src, dst, N, zchunk, k, uvel, stream);
 }
 
 template <typename S>

@@ -123,7 +123,9 @@ constexpr bool kAsyncStage = std::is_same<S, float>::value;
 // Raw staging of 2-byte storage (FP16, BF16) for even N: lanes 0..16 of a
 // row's warp copy the row of each population as 17 aligned 4-byte words, the
 // 34 elements from x0 - 2; thread `lane` reads element lane + 1.  Odd N (a
-// word would straddle the periodic wrap) reads global memory directly.
+// word would straddle the periodic wrap) reads global memory directly, in a
+// separate instantiation (template flag EVEN = false) so that the even-N code
+// carries neither the branch nor the registers of that path.
 template <typename S, int TY>
 struct RawStage16 {
     S raw[4][Q][TY + 2][34];
@@ -317,7 +319,7 @@ __device__ __forceinline__ int wrapc(int v, int n) {
 // ensemble kernel.  With VEL (FP32-computed storage) the tile also writes
 // rho0 u = sum xi f of the stored new state (Eq. 8) to uvel[3][N^3], summed in
 // population order.
-template <typename S, int TY, bool VEL = false>
+template <typename S, int TY, bool VEL = false, bool EVEN = true>
 __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restrict__ dst, int N,
                                            int bx, int by, int bz, int zchunk,
                                            const DugksCoef<typename Traits<S>::C>& kc,
@@ -348,25 +350,23 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
     auto zwrap = [&](int z) { return z < 0 ? z + N : (z >= N ? z - N : z); };
     auto rslot_of = [&](int z) { return (z - z0 + 4) & 3; };
 
-    // 2-byte staging: this lane's word starts at element x0 - 2 + 2 lane (even,
-    // so it never straddles the wrap when N is even)
-    const bool use16 = kStage16<S> && (N % 2 == 0);
+    // 2-byte staging (EVEN: the caller guarantees an even N): this lane's word
+    // starts at element x0 - 2 + 2 lane (even, so it never straddles the wrap)
+    constexpr bool use16 = kStage16<S> && EVEN;
     const size_t rowidx = (size_t)N * gy + (size_t)wrapc(x0 - 2 + 2 * lane, N);
 
     auto issue_plane = [&](int z) {
-        if constexpr (kStage16<S>) {
-            if (use16) {
-                if (lane <= 16) {
-                    const size_t o = (size_t)zwrap(z) * nn + rowidx;
-                    const int s = rslot_of(z);
+        if constexpr (use16) {
+            if (lane <= 16) {
+                const size_t o = (size_t)zwrap(z) * nn + rowidx;
+                const int s = rslot_of(z);
 #pragma unroll
-                    for (int i = 0; i < Q; ++i)
-                        if (KIN_CHECK(o + i * plane + 1 < Q * plane, DBG_DUGKS_LOAD, o + i * plane + 1) &&
-                            KIN_CHECK(s >= 0 && s < 4, DBG_DUGKS_SLOT, s))
-                            cp_async4(&stage16->raw[s][i][row][2 * lane], src + o + i * plane);
-                }
-                cp_async_commit();
+                for (int i = 0; i < Q; ++i)
+                    if (KIN_CHECK(o + i * plane + 1 < Q * plane, DBG_DUGKS_LOAD, o + i * plane + 1) &&
+                        KIN_CHECK(s >= 0 && s < 4, DBG_DUGKS_SLOT, s))
+                        cp_async4(&stage16->raw[s][i][row][2 * lane], src + o + i * plane);
             }
+            cp_async_commit();
         }
         if constexpr (kAsyncStage<S>) {
             const size_t o = (size_t)zwrap(z) * nn + colidx;
@@ -383,14 +383,11 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
         if constexpr (kAsyncStage<S>) {
             const int s = rslot_of(z);
             return pmk(stage->raw[s][2 * q + 1][row][lane], stage->raw[s][2 * q + 2][row][lane]);
+        } else if constexpr (use16) {
+            const int s = rslot_of(z);
+            return pmk(to_float(stage16->raw[s][2 * q + 1][row][lane + 1]),
+                       to_float(stage16->raw[s][2 * q + 2][row][lane + 1]));
         } else {
-            if constexpr (kStage16<S>) {
-                if (use16) {
-                    const int s = rslot_of(z);
-                    return pmk(to_float(stage16->raw[s][2 * q + 1][row][lane + 1]),
-                               to_float(stage16->raw[s][2 * q + 2][row][lane + 1]));
-                }
-            }
             const size_t o = (size_t)zwrap(z) * nn + colidx;
             if (!KIN_CHECK(o + (2 * q + 2) * plane < Q * plane, DBG_DUGKS_LOAD, o + (2 * q + 2) * plane))
                 return pmk(C(0), C(0));
@@ -400,10 +397,9 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
     auto raw_rest = [&](int z) -> C {
         if constexpr (kAsyncStage<S>) {
             return stage->raw[rslot_of(z)][0][row][lane];
+        } else if constexpr (use16) {
+            return to_float(stage16->raw[rslot_of(z)][0][row][lane + 1]);
         } else {
-            if constexpr (kStage16<S>) {
-                if (use16) return to_float(stage16->raw[rslot_of(z)][0][row][lane + 1]);
-            }
             const size_t o = (size_t)zwrap(z) * nn + colidx;
             if (!KIN_CHECK(o < plane, DBG_DUGKS_LOAD, o)) return C(0);
             return Traits<S>::load(src + o);
@@ -475,7 +471,7 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
     // the same warp
     auto wait_copies = [&]() {
         cp_async_wait_all();
-        if constexpr (kStage16<S>) __syncwarp();
+        if constexpr (use16) __syncwarp();
     };
     issue_plane(z0 - 1);
     issue_plane(z0);
@@ -508,7 +504,7 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
         __syncthreads();  // fy of plane z - 1 complete; my of plane z - 1 consumed
         Rec<C> Py;
         if (!last) {
-            if constexpr (kAsyncStage<S> || kStage16<S>) wait_copies();
+            if constexpr (kAsyncStage<S> || use16) wait_copies();
             prestep(z + 1, s_p1);
             if (z + 2 <= zend) issue_plane(z + 2);
             CellView<C> v;
@@ -611,11 +607,12 @@ __device__ __forceinline__ void dugks_tile(const S* __restrict__ src, S* __restr
                     // f-tilde-plus = 4/3 fbp - 1/3 f-tilde (Eq. 20), minus dt times the flux sum (Eq. 9)
                     const P2 t = pfma(kc.third, psub(xb, raw_pair(z - 1, PP)), xb);
                     const P2 o = pfma(kc.dts, Dprev[PP], t);
-                    Traits<S>::store(dst + (2 * PP + 1) * plane + c, o.x);
-                    Traits<S>::store(dst + (2 * PP + 2) * plane + c, o.y);
+                    // both members rounded by one paired conversion for 2-byte storage
+                    [[maybe_unused]] const P2 r =
+                        Traits<S>::store2(dst + (2 * PP + 1) * plane + c, dst + (2 * PP + 2) * plane + c, o);
                     if constexpr (VEL) {
-                        vel_add(std::integral_constant<int, 2 * PP + 1>{}, Traits<S>::rt(o.x));
-                        vel_add(std::integral_constant<int, 2 * PP + 2>{}, Traits<S>::rt(o.y));
+                        vel_add(std::integral_constant<int, 2 * PP + 1>{}, r.x);
+                        vel_add(std::integral_constant<int, 2 * PP + 2>{}, r.y);
                     }
                 });
                 const C xb0 = sm.ring0[s_m1][row][lane];

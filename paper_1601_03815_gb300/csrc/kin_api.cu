@@ -221,7 +221,7 @@ int launch_step(kin_sim* s, float* uvel = nullptr) {
     else if (s->variant == 1)
         e = dugks_step(s->storage, src, dst, s->fbp, s->N, s->nu, s->dt, s->block_dugks, s->stream);
     else
-        e = dugks_step_fused(s->storage, src, dst, s->N, s->nu, s->dt, s->tile_y,
+        e = dugks_step_fused(s->storage, src, dst, s->N, s->nu, s->dt, fused_tile_y(s),
                              s->zchunk > 0 ? s->zchunk : auto_zchunk(s), s->stream, uvel);
     if (e != cudaSuccess) return fail(KIN_ECUDA, "step launch: %s", cudaGetErrorString(e));
     s->launches += kin_step_launches(s);

@@ -61,6 +61,13 @@ struct Traits<float> {
     static __device__ __forceinline__ void store(float* p, C v) { *p = v; }
     // the value a store followed by a load returns
     static __device__ __forceinline__ C rt(C v) { return v; }
+    // stores the two members of a pair to p0, p1; returns what loads would return
+    template <typename P>
+    static __device__ __forceinline__ P store2(float* p0, float* p1, P v) {
+        *p0 = v.x;
+        *p1 = v.y;
+        return v;
+    }
 };
 template <>
 struct Traits<double> {
@@ -68,6 +75,12 @@ struct Traits<double> {
     static __device__ __forceinline__ C load(const double* p) { return __ldg(p); }
     static __device__ __forceinline__ void store(double* p, C v) { *p = v; }
     static __device__ __forceinline__ C rt(C v) { return v; }
+    template <typename P>
+    static __device__ __forceinline__ P store2(double* p0, double* p1, P v) {
+        *p0 = v.x;
+        *p1 = v.y;
+        return v;
+    }
 };
 template <>
 struct Traits<__half> {
@@ -75,6 +88,14 @@ struct Traits<__half> {
     static __device__ __forceinline__ C load(const __half* p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ void store(__half* p, C v) { *p = __float2half_rn(v); }
     static __device__ __forceinline__ C rt(C v) { return __half2float(__float2half_rn(v)); }
+    // one paired round-to-nearest conversion, the same rounding as two single ones
+    template <typename P>
+    static __device__ __forceinline__ P store2(__half* p0, __half* p1, P v) {
+        const __half2 h = __floats2half2_rn(v.x, v.y);
+        *p0 = __low2half(h);
+        *p1 = __high2half(h);
+        return P{__low2float(h), __high2float(h)};
+    }
 };
 template <>
 struct Traits<__nv_bfloat16> {
@@ -84,6 +105,13 @@ struct Traits<__nv_bfloat16> {
     }
     static __device__ __forceinline__ void store(__nv_bfloat16* p, C v) { *p = __float2bfloat16_rn(v); }
     static __device__ __forceinline__ C rt(C v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+    template <typename P>
+    static __device__ __forceinline__ P store2(__nv_bfloat16* p0, __nv_bfloat16* p1, P v) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+        *p0 = __low2bfloat16(h);
+        *p1 = __high2bfloat16(h);
+        return P{__low2float(h), __high2float(h)};
+    }
 };
 
 // ---------------------------------------------------------------------------
