@@ -261,12 +261,16 @@ const char* kin_last_error(void);
 void kin_destroy(kin_sim* sim);
 
 /* ------------------------------------------------------------------------
- * Ensembles: many independent simulations (any mix of N and scheme, all
- * KIN_F32 storage, one device) advanced together by ONE persistent,
- * cooperative kernel launch per kin_ensemble_step call, captured in a CUDA
- * graph.  Each member's results are bitwise identical to stepping it alone
- * with the same tile shape (kin_set_tuning tile_y / zchunk).  There is no
- * counterpart of this batching in the paper, which runs one simulation.
+ * Ensembles: many independent simulations (any mix of N and scheme; KIN_F32,
+ * KIN_F16 or KIN_BF16 storage, 2-byte DUGKS members with even N; one device)
+ * advanced together by ONE CUDA graph launch per kin_ensemble_step call: a
+ * persistent, cooperative kernel runs every step of the DUGKS members, and,
+ * on a parallel stream of the same graph, one batched launch per step and
+ * storage type updates all LBE members, its blocks sharing the SMs with the
+ * DUGKS blocks.  Each member's results are bitwise identical to stepping it
+ * alone (DUGKS: with the same tile shape, kin_set_tuning tile_y / zchunk).
+ * There is no counterpart of this batching in the paper, which runs one
+ * simulation.
  */
 typedef struct kin_ensemble kin_ensemble;
 
@@ -274,22 +278,29 @@ typedef struct kin_ensemble kin_ensemble;
  * keeps ownership and must destroy the ensemble before any member). */
 int kin_ensemble_create(kin_sim* const* members, int n, kin_ensemble** out);
 
-/* Work decomposition: tile_y (4 or 8) and zchunk of the DUGKS tiles, lbe_nodes
- * (multiple of 32) LBE nodes per work item; values <= 0 keep the setting. */
-int kin_ensemble_set_tuning(kin_ensemble* ens, int tile_y, int zchunk, int lbe_nodes);
+/* Work decomposition: tile_y (4, 6 or 8; default 6 when the ensemble holds
+ * both schemes, so that LBE blocks fit beside each DUGKS block, else 8) and
+ * zchunk of the DUGKS tiles, lbe_block (a multiple of 32, at most 128) threads
+ * per block of the batched LBE launches; values <= 0 keep the setting. */
+int kin_ensemble_set_tuning(kin_ensemble* ens, int tile_y, int zchunk, int lbe_block);
 
-/* Advance every member by nsteps in one persistent launch (synchronous).
- * Members must be idle; their streams are synchronised first.  Returns
- * KIN_ETIMEOUT if a member barrier inside the kernel waited longer than its
- * bound (the members are then left at their state before the call). */
+/* Advance every member by nsteps (synchronous): one graph launch, or one per
+ * 256 steps when there are LBE members (a graph holds one LBE launch per
+ * step).  Members must be idle; their streams are synchronised first.
+ * Returns KIN_ETIMEOUT if a member barrier inside the persistent kernel waited
+ * longer than its bound; every member's state is then undefined and the
+ * member returns KIN_ESTATE from any call that reads or steps it until its
+ * state is set again (kin_set_f, kin_set_velocity, kin_init_field). */
 int kin_ensemble_step(kin_ensemble* ens, int nsteps);
 
-/* Run the persistent kernel with a member barrier that cannot be satisfied
- * and a wait bound of `seconds`: must return KIN_ETIMEOUT promptly and leave
- * the members unchanged.  For testing the bounded wait. */
+/* Run the persistent kernel alone with a member barrier that cannot be
+ * satisfied and a wait bound of `seconds`: must return KIN_ETIMEOUT promptly,
+ * with every member then refusing work (KIN_ESTATE) until set again.  For
+ * testing the bounded wait; KIN_EINVAL without DUGKS members. */
 int kin_ensemble_test_timeout(kin_ensemble* ens, double seconds);
 
-/* Work items per step, thread blocks of the persistent launch, launches so far. */
+/* Work per step (DUGKS tiles + batched LBE thread blocks), thread blocks of
+ * the persistent launch (0 without DUGKS members), graph launches so far. */
 int kin_ensemble_info(const kin_ensemble* ens, int* nitems, int* grid, int64_t* launches);
 
 void kin_ensemble_destroy(kin_ensemble* ens);

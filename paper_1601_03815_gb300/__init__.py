@@ -338,9 +338,11 @@ class Sim:
 
 
 class Ensemble:
-    """Independent simulations advanced together by one persistent kernel
-    launch per step() call (see kin_ensemble_* in kin.h).  Keeps references to
-    its members so they outlive it."""
+    """Independent simulations advanced together by one CUDA graph launch per
+    step() call: a persistent kernel for the DUGKS members and, on a parallel
+    stream, one batched launch per step for the LBE members (see
+    kin_ensemble_* in kin.h).  Keeps references to its members so they
+    outlive it."""
 
     def __init__(self, members):
         self.members = list(members)
@@ -349,8 +351,8 @@ class Ensemble:
         _check(lib().kin_ensemble_create(arr, len(self.members), ctypes.byref(h)), "kin_ensemble_create")
         self._h = h
 
-    def set_tuning(self, tile_y: int = 0, zchunk: int = 0, lbe_nodes: int = 0):
-        _check(lib().kin_ensemble_set_tuning(self._h, int(tile_y), int(zchunk), int(lbe_nodes)),
+    def set_tuning(self, tile_y: int = 0, zchunk: int = 0, lbe_block: int = 0):
+        _check(lib().kin_ensemble_set_tuning(self._h, int(tile_y), int(zchunk), int(lbe_block)),
                "kin_ensemble_set_tuning")
 
     def step(self, n: int = 1):

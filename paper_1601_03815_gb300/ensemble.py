@@ -1,6 +1,8 @@
 """Batched ensembles: independent DHIT realisations of uneven N advanced by one
-persistent kernel launch per call, with an autotuner for the work
-decomposition (DUGKS plane-tile height and z chunk, LBE nodes per work item).
+CUDA graph launch per call (a persistent kernel for the DUGKS members, beside
+it one batched launch per step for the LBE members), with an autotuner for
+the work decomposition (DUGKS plane-tile height and z chunk, threads per block
+of the batched LBE launches).
 
 The reference ensemble has 24 members, 8 x 32^3, 8 x 64^3, 6 x 96^3 and
 2 x 128^3, each with its own seed, a seeded coin for the scheme, Ma = 0.1 and
@@ -24,9 +26,9 @@ import numpy as np
 from . import DUGKS, F32, LBE_MRT, Ensemble, Sim
 
 REFERENCE_SIZES = ((32, 8), (64, 8), (96, 6), (128, 2))
-TUNE_TILE_Y = (4, 8)
+TUNE_TILE_Y = (4, 6, 8)
 TUNE_ZCHUNK = (8, 16, 32, 64, 128)
-TUNE_LBE_NODES = (1024, 4096, 16384)
+TUNE_LBE_BLOCK = (64, 128)
 
 
 def member_specs(sizes=REFERENCE_SIZES, seed: int = 1400, re_range=(20.0, 40.0)):
@@ -61,11 +63,12 @@ def _signature(sims):
 
     dev = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
     sizes = sorted((s.N, s.scheme) for s in sims)
-    return "%s|%s" % (dev, ",".join("%d%s" % (n, "L" if sc == LBE_MRT else "D") for n, sc in sizes))
+    # "c": tunings of the batched-LBE form (threads per LBE block, 6-row tiles)
+    return "c|%s|%s" % (dev, ",".join("%d%s" % (n, "L" if sc == LBE_MRT else "D") for n, sc in sizes))
 
 
 def autotune(ens: Ensemble, steps: int = 10, use_cache: bool = True, verbose: bool = False):
-    """Time every (tile_y, zchunk, lbe_nodes) candidate on this ensemble and
+    """Time every (tile_y, zchunk, lbe_block) candidate on this ensemble and
     leave the fastest set.  The members advance while tuning.  Results are
     cached per device and member mix."""
     sig = _signature(ens.members)
@@ -82,7 +85,7 @@ def autotune(ens: Ensemble, steps: int = 10, use_cache: bool = True, verbose: bo
         ens.set_tuning(*best["tuning"])
         return best
     timings = []
-    for ty, zc, ln in itertools.product(TUNE_TILE_Y, TUNE_ZCHUNK, TUNE_LBE_NODES):
+    for ty, zc, ln in itertools.product(TUNE_TILE_Y, TUNE_ZCHUNK, TUNE_LBE_BLOCK):
         ens.set_tuning(ty, zc, ln)
         ens.step(2)  # capture the graph and warm up
         t0 = time.perf_counter()
@@ -90,7 +93,7 @@ def autotune(ens: Ensemble, steps: int = 10, use_cache: bool = True, verbose: bo
         dt = time.perf_counter() - t0
         timings.append((dt, (ty, zc, ln)))
         if verbose:
-            print("tile_y=%d zchunk=%d lbe_nodes=%d: %.3f ms/step" % (ty, zc, ln, 1e3 * dt / steps))
+            print("tile_y=%d zchunk=%d lbe_block=%d: %.3f ms/step" % (ty, zc, ln, 1e3 * dt / steps))
     dt, tuning = min(timings)
     ens.set_tuning(*tuning)
     best = {"tuning": list(tuning), "ms_per_step": 1e3 * dt / steps,
@@ -122,9 +125,11 @@ def measure(steps: int = 500, seed: int = 1400, tune: bool = True, verbose: bool
     for s, (N, scheme, sd, re) in zip(sims, specs):
         s.init_field(sd, 4.0, re)
     torch.cuda.synchronize()
+    launches0 = ens.info()["launches"]
     t0 = time.perf_counter()
     ens.step(steps)
     t_batched = time.perf_counter() - t0
+    graph_launches = ens.info()["launches"] - launches0
     stats = [s.stats() for s in sims]
     # the same members one by one with kin_step (their own launches)
     for s, (N, scheme, sd, re) in zip(sims, specs):
@@ -147,7 +152,10 @@ def measure(steps: int = 500, seed: int = 1400, tune: bool = True, verbose: bool
         "batched_s": t_batched,
         "one_by_one_mlups": cells * steps / t_plain / 1e6,
         "one_by_one_s": t_plain,
-        "launches": 1, "graph": True, "tuning": tuned["tuning"] if tuned else None,
+        "graph_launches": graph_launches,
+        "kernels": {"persistent_dugks_per_graph": 1 if any(sp[1] == DUGKS for sp in specs) else 0,
+                    "batched_lbe_per_step": 1 if any(sp[1] == LBE_MRT for sp in specs) else 0},
+        "graph": True, "tuning": tuned["tuning"] if tuned else None,
         "items_per_step": info["items"], "blocks": info["grid"],
         "schemes": {"lbe": sum(1 for sp in specs if sp[1] == LBE_MRT),
                     "dugks": sum(1 for sp in specs if sp[1] == DUGKS)},

@@ -65,7 +65,7 @@ def main():
         members.append(sim)
         refs.append(oracle.step(scheme, oracle.step(scheme, f, 0.015, dt), 0.015, dt))
     ens = kin.Ensemble(members)
-    ens.set_tuning(tile_y=4, zchunk=3, lbe_nodes=64)
+    ens.set_tuning(tile_y=4, zchunk=3, lbe_block=64)
     ens.step(2)
     e = max(err(m.get_f(), r) for m, r in zip(members, refs))
     ens.close()

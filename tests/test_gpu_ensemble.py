@@ -1,9 +1,10 @@
-"""Persistent-kernel ensemble: each member matches stepping it alone with
-kin_step (within the FP32 parity tolerance: the two kernels contract the same
-node arithmetic into FMAs differently), is bitwise identical whether it runs
-alone in an ensemble or mixed with other members, across odd and even step
-counts, graph re-launches and ragged tiles; the in-kernel member barrier is
-bounded and reports KIN_ETIMEOUT without touching state."""
+"""Ensembles (persistent DUGKS kernel beside batched LBE launches, one graph):
+each member is bitwise identical to stepping it alone with kin_step and
+whether it runs alone in an ensemble or mixed with other members, across odd
+and even step counts, graph re-launches, graphs split at 256 steps, ragged
+tiles and FP32/FP16/BF16 storage; members match the FP64 oracle; the member
+barrier is bounded and reports KIN_ETIMEOUT, after which members refuse work
+until set."""
 import numpy as np
 import pytest
 
@@ -36,11 +37,12 @@ def _make(kin, orc, tuning=(8, 16)):
     return ens_members, solo
 
 
-@pytest.mark.parametrize("tuning", [(8, 16), (4, 7)])
+@pytest.mark.parametrize("tuning", [(8, 16), (4, 7), (6, 16)])
 def test_ensemble_is_bitwise_equal_to_solo_runs(kin, orc, tuning):
-    members, solo = _make(kin, orc, tuning)
+    # a solo run has no 6-row tiles; a cell's arithmetic does not depend on the tile
+    members, solo = _make(kin, orc, (8, 16) if tuning[0] == 6 else tuning)
     ens = kin.Ensemble(members)
-    ens.set_tuning(tile_y=tuning[0], zchunk=tuning[1], lbe_nodes=256)
+    ens.set_tuning(tile_y=tuning[0], zchunk=tuning[1], lbe_block=128)
     ens.step(3)
     ens.step(4)  # second launch, other parity
     ens.step(3)  # graph for 3 steps reused
@@ -48,9 +50,7 @@ def test_ensemble_is_bitwise_equal_to_solo_runs(kin, orc, tuning):
         s.step(10)
     for a, b in zip(members, solo):
         assert a.steps_taken == 10
-        fa, fb = a.get_f(), b.get_f()
-        scale = np.abs(fb).reshape(19, -1).max(axis=1)
-        assert (np.abs(fa - fb).reshape(19, -1).max(axis=1) / scale).max() < 1e-5
+        np.testing.assert_array_equal(a.get_f(), b.get_f())
     info = ens.info()
     assert info["launches"] == 3 and info["grid"] >= 1 and info["items"] > len(MEMBERS)
     ens.close()
@@ -73,7 +73,7 @@ def test_ensemble_members_match_the_oracle(kin, orc):
         members.append((sim, scheme, nu, dt))
         states.append(sim.get_f())  # the stored FP32 state the GPU steps from
     ens = kin.Ensemble([m[0] for m in members])
-    ens.set_tuning(tile_y=4, zchunk=5, lbe_nodes=256)
+    ens.set_tuning(tile_y=4, zchunk=5, lbe_block=128)
     ens.step(2)
     ens.step(1)
     for (sim, scheme, nu, dt), f in zip(members, states):
@@ -142,12 +142,85 @@ def test_member_alone_and_in_the_mix_are_bitwise_equal(kin, orc):
     mix.close()
 
 
+def test_mixed_storage_members_are_bitwise_equal_to_solo_runs(kin, orc):
+    """FP16 and BF16 members (LBE at N % 4 == 0, N % 4 == 2 and odd N; DUGKS at
+    even N) beside FP32 ones: bitwise the solo kin_step result."""
+    specs = [("lbe", 16, kin.F16), ("lbe", 18, kin.BF16), ("lbe", 9, kin.F16), ("dugks", 16, kin.F16),
+             ("dugks", 14, kin.BF16), ("dugks", 12, kin.F32), ("lbe", 12, kin.F32)]
+    members, solo = [], []
+    for k, (scheme, N, st) in enumerate(specs):
+        f0 = _state(orc, N, 500 + k)
+        sc = kin.LBE_MRT if scheme == "lbe" else kin.DUGKS
+        dt = 1.0 if scheme == "lbe" else 0.45
+        a = kin.Sim(N, sc, 0.012 + 0.001 * k, 0.1, dt, st)
+        b = kin.Sim(N, sc, 0.012 + 0.001 * k, 0.1, dt, st)
+        a.set_f(f0)
+        b.set_f(f0)
+        b.set_tuning(tile_y=8, zchunk=5)
+        members.append(a)
+        solo.append(b)
+    ens = kin.Ensemble(members)
+    ens.set_tuning(tile_y=8, zchunk=5)
+    ens.step(2)
+    ens.step(3)
+    for s in solo:
+        s.step(5)
+    for a, b in zip(members, solo):
+        np.testing.assert_array_equal(a.get_f(), b.get_f())
+    ens.close()
+    for s in members + solo:
+        s.close()
+
+
+@pytest.mark.parametrize("schemes", ["lbe", "dugks"])
+def test_single_scheme_ensembles_and_long_calls(kin, orc, schemes):
+    """An ensemble of one scheme (no fork in the graph; an LBE-only one has no
+    persistent launch) and a call of 300 steps (two graphs when there are LBE
+    members) give the solo results bitwise."""
+    Ns = (10, 16, 7)
+    members, solo = [], []
+    for k, N in enumerate(Ns):
+        f0 = _state(orc, N, 700 + k)
+        sc = kin.LBE_MRT if schemes == "lbe" else kin.DUGKS
+        dt = 1.0 if schemes == "lbe" else 0.45
+        a = kin.Sim(N, sc, 0.02, 0.1, dt, kin.F32)
+        b = kin.Sim(N, sc, 0.02, 0.1, dt, kin.F32)
+        a.set_f(f0)
+        b.set_f(f0)
+        members.append(a)
+        solo.append(b)
+    ens = kin.Ensemble(members)
+    steps = 300
+    ens.step(steps)
+    for s in solo:
+        s.set_tuning(tile_y=8, zchunk=16)
+        s.step(steps)
+    for a, b in zip(members, solo):
+        assert a.steps_taken == steps
+        np.testing.assert_array_equal(a.get_f(), b.get_f())
+    info = ens.info()
+    assert info["launches"] == (2 if schemes == "lbe" else 1)
+    assert (info["grid"] == 0) == (schemes == "lbe")
+    if schemes == "lbe":
+        assert ens.test_timeout(0.05) == kin.KIN_EINVAL
+    ens.close()
+    for s in members + solo:
+        s.close()
+
+
 def test_ensemble_rejects_bad_members(kin):
-    a = kin.Sim(8, kin.LBE_MRT, 0.01, 0.1, 1.0, kin.F16)
+    a = kin.Sim(8, kin.LBE_MRT, 0.01, 0.1, 1.0, kin.F64)
     with pytest.raises(kin.KinError):
         kin.Ensemble([a])
     b = kin.Sim(8, kin.LBE_MRT, 0.01, 0.1, 1.0, kin.F32)
     with pytest.raises(kin.KinError):
         kin.Ensemble([b, b])
-    a.close()
-    b.close()
+    c = kin.Sim(9, kin.DUGKS, 0.01, 0.1, 0.5, kin.F16)  # 2-byte DUGKS needs an even N
+    with pytest.raises(kin.KinError):
+        kin.Ensemble([b, c])
+    ens = kin.Ensemble([b])
+    with pytest.raises(kin.KinError):
+        ens.set_tuning(lbe_block=256)
+    ens.close()
+    for s in (a, b, c):
+        s.close()
