@@ -249,7 +249,7 @@ def cpu_model() -> str:
 def cpu_baseline_sample(steps: int = 1):
     """The FP64 oracle (as it stands) on the host cores, on the 128^3
     workloads of the CPU-baseline plan: C2 (k0 = 8, Ma = 0.1, Re_lambda = 25,
-    seed 1200) and the paper-parity P1 (the Sec. IV.C field shape, u' = 0.032,
+    seed 1200) and the paper-parity P1 (the Table I field of Sec. IV.A, u' = 0.032,
     nu = 1.2395e-2 of Table I), `steps` MRT-LBE and `steps` DUGKS (dt = 0.5)
     steps each, with all host cores and with 16 threads (the paper's 16 MPI
     cores).  The headline value is C2 with all cores."""
@@ -285,13 +285,13 @@ def cpu_baseline_sample(steps: int = 1):
     value = 2.0 / (1.0 / head["lbe_mlups"] + 1.0 / head["dugks_mlups"])
     return {"value": value, "unit": "MLUPS", "cores": nproc, "kind": "oracle", "cpu": cpu_model(),
             "nproc": nproc,
-            "sample": "FP64 oracle, 128^3: C2 (k0=8, Ma=0.1, Re_lambda=25) and P1 (Sec. IV.C field, "
+            "sample": "FP64 oracle, 128^3: C2 (k0=8, Ma=0.1, Re_lambda=25) and P1 (Table I field, "
                       "u'=0.032, nu=1.2395e-2), %d MRT-LBE + %d DUGKS steps each, at %s threads; value = "
                       "C2 at all %d cores, one LBE + one DUGKS step per update pair" % (
                           steps, steps, " and ".join(str(t) for t in threads), nproc),
             "runs": runs,
             "paper": {"lbe_mlups": 128 ** 3 / 0.666 / 1e6, "dugks_mlups": 128 ** 3 / 0.911 / 1e6,
-                      "hardware": "16 CPU cores, MPI (Sec. IV.D)"}}
+                      "hardware": "16 CPU cores, MPI (Sec. IV.E)"}}
 
 
 def extras(args) -> dict:

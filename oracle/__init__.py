@@ -209,8 +209,8 @@ def lbe_consistent(u0, nu: float, iters: int, drho0=None):
 
 
 def dugks_consistent_step(f, u0, nu: float, dt: float) -> np.ndarray:
-    """One iteration of the consistent initialisation for DUGKS (Sec. IV.A:
-    "as for the LBE and DUGKS methods", after Mei et al.): the DUGKS step of
+    """One iteration of the consistent initialisation for DUGKS (Sec. IV.A
+    applies the procedure of Mei et al. to both schemes): the DUGKS step of
     Eqs. 9-20, after which the momentum of the new f-tilde is set back to
     rho0 u0 along the linear term of the equilibrium (Eq. 7),
     f-tilde_i += 3 W_i xi_i . rho0 (u0 - u), which changes neither the mass

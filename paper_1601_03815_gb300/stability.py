@@ -1,5 +1,5 @@
 """Maximum stable Taylor-microscale Reynolds number of MRT-LBE and DUGKS on a
-fixed mesh (Sec. V: the paper raises Re_lambda at 128^3, DUGKS at CFL 0.9,
+fixed mesh (Sec. IV.E: the paper raises Re_lambda at 128^3, DUGKS at CFL 0.9,
 until a code blows up, without regard to accuracy).
 
 For each Re_lambda of an increasing list the seeded initial field (spectrum

@@ -14,14 +14,14 @@ file starts with a header naming the case and this command.
 Cases
   lbe256  256^3, k0 = 8, Ma = 0.15, Re_lambda = 70, seed 1300: MRT-LBE E and
           eps every 5 steps until the state is non-finite (the 256^3 timing
-          field, whose LBE run blows up; Sec. IV.D discusses LBE stability).
+          field, whose LBE run blows up; Sec. IV.E discusses LBE stability).
   c2      128^3, k0 = 8, Ma = 0.1, Re_lambda = 25, seed 1200, 2000 steps of
           the named scheme (DUGKS dt = 0.5): E and eps every 10 steps, E(k)
           every 200 steps.
   c3      64^3 version of the 256^3 timing field: k0 = 8, Ma = 0.15,
           Re_lambda = 70, seed 1300, 1000 steps (DUGKS dt = 0.5), E and eps
           every 10 steps, E(k) every 200 steps, until non-finite.
-  f3      64^3 box of the Sec. IV.C decay workload: spectrum shape
+  f3      64^3 box of the Sec. IV.D decay workload: spectrum shape
           k^4 exp(-0.14 k^2) (k0 = sqrt(2/0.14)), u' = 0.032 (Ma = u'/c_s),
           seed 1700, nu from the named Re_lambda (52.12 or 104.24); 400
           lattice time units (MRT-LBE dt = 1, DUGKS dt = 0.5), E and eps

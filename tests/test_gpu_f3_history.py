@@ -1,4 +1,4 @@
-"""Decay histories of the second workload (Sec. IV.C, Re_lambda = 52.12 and
+"""Decay histories of the second workload (Sec. IV.D, Re_lambda = 52.12 and
 104.24) against stored FP64 oracle runs.
 
 The stored files under tests/golden/ (oracle_f3_64_<scheme>_re<Re>.txt) were

@@ -261,7 +261,7 @@ def test_errors_and_edge_cases(kin):
 
 
 @pytest.mark.parametrize("case", [
-    # DUGKS at CFL 0.9, the stability sweep's time step (Sec. IV.D): dt = 0.9 / sqrt(2)
+    # DUGKS at CFL 0.9, the stability sweep's time step (Sec. IV.E): dt = 0.9 / sqrt(2)
     ("dugks", 0.9 / np.sqrt(2.0), 0.013),
     ("dugks", 0.9 / np.sqrt(2.0), 2e-7),
     # the sweep's smallest viscosities: tau = 3 nu = 6e-7 for DUGKS (c1 = 1 - c2
