@@ -285,3 +285,26 @@ def test_one_step_parity_sweep_regime(kin, orc, case, storage, N):
     ref = orc.step(scheme, f_in, nu, dt)
     assert _err(got, ref) < TOL[storage]
     sim.close()
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2])
+def test_lbe_block_sizes_above_the_launch_bounds(kin, storage):
+    """block_x beyond the LBE kernels' 256 threads is clamped, not a failed
+    launch: N = 264 (FP32: one cell a thread; FP16/BF16: four cells, N % 4 == 0)
+    and N = 262 (two cells) give the default block's results bit for bit."""
+    import kin_inputs as ki
+
+    for N in (264, 262) if storage else (264,):
+        u = ki.random_velocity(N, N, N, 41, 0.03)
+        ref = kin.Sim(N, kin.LBE_MRT, 0.02, 0.1, 1.0, storage)
+        ref.set_velocity(u)
+        ref.step(2)
+        want = ref.sample_f(list(range(0, N ** 3, 9973)))
+        ref.close()
+        for bx in (512, 1024):
+            sim = kin.Sim(N, kin.LBE_MRT, 0.02, 0.1, 1.0, storage)
+            sim.set_tuning(block_x=bx)
+            sim.set_velocity(u)
+            sim.step(2)
+            np.testing.assert_array_equal(sim.sample_f(list(range(0, N ** 3, 9973))), want)
+            sim.close()
