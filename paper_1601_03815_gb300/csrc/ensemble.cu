@@ -15,11 +15,13 @@
 //
 // LBE members: one batched launch per step covers every LBE member of a
 // storage type (a block takes consecutive nodes of one member), on a second
-// stream of the same graph.  Its blocks (48 registers a thread, no shared
-// memory) run beside the one 200 KB DUGKS block of each SM, so the
-// memory-bound LBE nodes use the bandwidth and issue slots that the
-// issue-bound DUGKS tiles leave.  The two kernels never wait on each other;
-// consecutive LBE steps are ordered by their stream.
+// stream of the same graph.  With both schemes present the persistent kernel
+// runs 6-row tiles (8 warps, 160 KB of shared memory, at most 160 registers
+// a thread), which leave room for three 4-warp FP32 LBE blocks (56 registers
+// a thread, no shared memory) on each SM: the memory-bound LBE nodes use the
+// bandwidth and issue slots that the issue-bound DUGKS tiles leave.  The two
+// kernels never wait on each other; consecutive LBE steps are ordered by
+// their stream.
 //
 // Which block runs an item does not change what it computes: a member's
 // results are bitwise those of stepping it alone.
