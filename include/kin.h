@@ -264,14 +264,14 @@ void kin_destroy(kin_sim* sim);
 /* ------------------------------------------------------------------------
  * Ensembles: many independent simulations (any mix of N and scheme; KIN_F32,
  * KIN_F16 or KIN_BF16 storage, 2-byte DUGKS members with even N; one device)
- * advanced together by ONE CUDA graph launch per kin_ensemble_step call: a
- * persistent, cooperative kernel runs every step of the DUGKS members, and,
- * on a parallel stream of the same graph, one batched launch per step and
- * storage type updates all LBE members, its blocks sharing the SMs with the
- * DUGKS blocks.  Each member's results are bitwise identical to stepping it
- * alone (DUGKS: with the same tile shape, kin_set_tuning tile_y / zchunk).
- * There is no counterpart of this batching in the paper, which runs one
- * simulation.
+ * advanced together by ONE CUDA graph launch per kin_ensemble_step call (per
+ * 256 steps when there are LBE members): a persistent, cooperative kernel
+ * runs every step of the DUGKS members, and, on a parallel stream of the same
+ * graph, one batched launch per step and storage type updates all LBE
+ * members, its blocks sharing the SMs with the DUGKS blocks.  Each member's
+ * results are bitwise identical to stepping it alone with kin_step (a cell's
+ * arithmetic does not depend on the tile shape or the launch).  There is no
+ * counterpart of this batching in the paper, which runs one simulation.
  */
 typedef struct kin_ensemble kin_ensemble;
 
