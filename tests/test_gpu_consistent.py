@@ -56,7 +56,7 @@ def test_converged_density_is_the_taylor_green_pressure(kin):
 @pytest.mark.parametrize("storage,tol", [(3, 1e-12), (0, 1e-5)])
 @pytest.mark.parametrize("N", [16, 15])
 def test_dugks_iterations_match_the_oracle(kin, orc, storage, tol, N):
-    """DUGKS (Sec. IV.A: "as for the LBE and DUGKS methods"): a plain step
+    """DUGKS (Sec. IV.A applies the procedure to both schemes): a plain step
     and the momentum set back to rho0 u0, 40 iterations against the oracle."""
     dt = 0.5
     u = ki.random_velocity(N, N, N, 950 + N, 0.03)
@@ -100,3 +100,25 @@ def test_bad_arguments_are_rejected(kin):
             sim.init_consistent(0)
         assert e.value.code == kin.KIN_EINVAL
         sim.close()
+
+
+@pytest.mark.parametrize("scheme", ["lbe", "dugks"])
+@pytest.mark.parametrize("storage,u_round", [(1, 2.0 ** -11), (2, 2.0 ** -8)])
+def test_iterations_with_two_byte_storage(kin, orc, scheme, storage, u_round):
+    """FP16 / BF16 storage: each iteration stores the state, rounding every
+    value by at most u |f_i| (unit roundoff u).  The held momentum resets the
+    rounding of j each iteration; the rest evolves slowly and its rounding
+    errors add as a random walk, so after n iterations the distance to the
+    FP64 oracle iteration stays within 4 sqrt(n) u of max |f_i| (four standard
+    deviations of that walk, plus the initial rounding)."""
+    N, n = 16, 40
+    dt = 1.0 if scheme == "lbe" else 0.5
+    u = ki.random_velocity(N, N, N, 970 + storage, 0.03)
+    sim = kin.Sim(N, kin.LBE_MRT if scheme == "lbe" else kin.DUGKS, NU, 0.1, dt, storage)
+    sim.set_velocity(u)
+    iters, res = sim.init_consistent(n, -1.0)
+    assert iters == n and np.isfinite(res)
+    ref, _ = orc.lbe_consistent(u, NU, n) if scheme == "lbe" else orc.dugks_consistent(u, NU, dt, n)
+    err = _err(sim.get_f(), ref)
+    assert err < 4.0 * np.sqrt(n) * u_round, err
+    sim.close()
