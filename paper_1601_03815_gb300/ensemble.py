@@ -163,13 +163,36 @@ def measure(steps: int = 500, seed: int = 1400, tune: bool = True, verbose: bool
     }
 
 
+def just_step(steps: int, tuning, seed: int = 1400):
+    """Build the reference ensemble, set `tuning` (tile_y, zchunk, lbe_block)
+    and advance it `steps` steps in one call, untimed (for profilers)."""
+    import torch
+
+    sims = make_members(member_specs(seed=seed))
+    ens = Ensemble(sims)
+    ens.set_tuning(*tuning)
+    ens.step(steps)
+    torch.cuda.synchronize()
+    info = ens.info()
+    ens.close()
+    for s in sims:
+        s.close()
+    return info
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--seed", type=int, default=1400)
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--verbose", action="store_true")
+    ap.add_argument("--just-step", type=int, default=0, metavar="K",
+                    help="only advance the reference ensemble K steps in one call (for profilers)")
+    ap.add_argument("--tuning", type=int, nargs=3, default=[6, 128, 128], metavar=("TILE_Y", "ZCHUNK", "LBE_BLOCK"))
     a = ap.parse_args()
+    if a.just_step > 0:
+        print(json.dumps(just_step(a.just_step, a.tuning, a.seed)))
+        return
     print(json.dumps(measure(a.steps, a.seed, not a.no_tune, a.verbose)))
 
 
