@@ -142,9 +142,11 @@ def test_member_alone_and_in_the_mix_are_bitwise_equal(kin, orc):
     mix.close()
 
 
-def test_mixed_storage_members_are_bitwise_equal_to_solo_runs(kin, orc):
+@pytest.mark.parametrize("tile_y", [6, 8])
+def test_mixed_storage_members_are_bitwise_equal_to_solo_runs(kin, orc, tile_y):
     """FP16 and BF16 members (LBE at N % 4 == 0, N % 4 == 2 and odd N; DUGKS at
-    even N) beside FP32 ones: bitwise the solo kin_step result."""
+    even N) beside FP32 ones: bitwise the solo kin_step result, with 6-row
+    tiles (the default beside LBE members) and 8-row ones."""
     specs = [("lbe", 16, kin.F16), ("lbe", 18, kin.BF16), ("lbe", 9, kin.F16), ("dugks", 16, kin.F16),
              ("dugks", 14, kin.BF16), ("dugks", 12, kin.F32), ("lbe", 12, kin.F32)]
     members, solo = [], []
@@ -160,7 +162,7 @@ def test_mixed_storage_members_are_bitwise_equal_to_solo_runs(kin, orc):
         members.append(a)
         solo.append(b)
     ens = kin.Ensemble(members)
-    ens.set_tuning(tile_y=8, zchunk=5)
+    ens.set_tuning(tile_y=tile_y, zchunk=5)
     ens.step(2)
     ens.step(3)
     for s in solo:
