@@ -465,28 +465,46 @@ def run_ours(args):
         pinned.numpy()[...] = u0
         hu = pinned.numpy()
         k_e2e = max(10, min(args.steps, SEGMENT))
-        # the two schemes as a user would run two independent simulations:
-        # each on its own stream (kin_create with no stream), so that one
-        # scheme's read-back overlaps the other's step
-        lbe_e = kin.Sim(N, kin.LBE_MRT, lbe.nu, MA, 1.0, st)
-        dug_e = kin.Sim(N, kin.DUGKS, dug.nu, MA, 0.5, st)
+        # the two schemes as a user would run two independent simulations,
+        # each on its own stream, monitoring E and eps every step: the
+        # statistics of step k are copied to page-locked host memory
+        # asynchronously and read (checked) once step k + 1 is enqueued
+        sl, sd = torch.cuda.Stream(), torch.cuda.Stream()
+        lbe_e = kin.Sim(N, kin.LBE_MRT, lbe.nu, MA, 1.0, st, stream=sl)
+        dug_e = kin.Sim(N, kin.DUGKS, dug.nu, MA, 0.5, st, stream=sd)
+        res = torch.zeros((k_e2e, 2, 2), dtype=torch.float64, pin_memory=True).numpy()
+
+        def e2e_steps(n):
+            done = []
+            for k in range(n):
+                lbe_e.step(1)
+                lbe_e.stats_async(res[k, 0])
+                # the fused DUGKS step also writes the velocity its statistics need
+                dug_e.step_stats_async(1, res[k, 1])
+                evs = (torch.cuda.Event(), torch.cuda.Event())
+                evs[0].record(sl)
+                evs[1].record(sd)
+                done.append(evs)
+                if k > 0:
+                    for ev in done[k - 1]:
+                        ev.synchronize()
+                    if not np.all(np.isfinite(res[k - 1])):
+                        raise RuntimeError("non-finite statistics at end-to-end step %d" % (k - 1))
+            lbe_e.sync()
+            dug_e.sync()
+            if not np.all(np.isfinite(res[n - 1])):
+                raise RuntimeError("non-finite statistics at end-to-end step %d" % (n - 1))
+
         lbe_e.set_velocity(hu)
         dug_e.set_velocity(hu)
-        lbe_e.step(1)
-        dug_e.step_stats(1)
-        lbe_e.stats()
+        e2e_steps(2)
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         lbe_e.set_velocity(hu)
         dug_e.set_velocity(hu)
-        for k in range(k_e2e):
-            # the LBE step runs while the DUGKS step and its statistics are
-            # waited for (kin_step_stats: the step also writes the velocity)
-            lbe_e.step(1)
-            dug_e.step_stats(1)
-            lbe_e.stats()
+        e2e_steps(k_e2e)
         torch.cuda.synchronize()
         te = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         lbe_e.close()
@@ -495,8 +513,9 @@ def run_ours(args):
                "h2d_bytes_per_step": int(2 * u0.nbytes / k_e2e), "d2h_bytes_per_step": 2 * 2 * 8,
                "steps": k_e2e,
                "what": "kin_set_velocity from pinned host memory for both schemes, then per step "
-                       "kin_step(1) of the LBE run, kin_step_stats(1, E, eps) of the DUGKS run and "
-                       "kin_stats(E, eps) of the LBE run, each simulation on its own stream; host "
+                       "kin_step(1) + kin_stats_async of the LBE run and kin_step_stats_async(1) of "
+                       "the DUGKS run, each simulation on its own stream; E and eps of both copied "
+                       "to page-locked host memory every step and checked one step later; host "
                        "wall clock"}
 
     # stability probe (untimed): first check at which E is non-finite, every 5

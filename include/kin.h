@@ -151,6 +151,22 @@ int kin_stats(kin_sim* sim, double* E, double* eps, double* Ek);
  * stream; errors as kin_step and kin_stats. */
 int kin_step_stats(kin_sim* sim, int n, double* E, double* eps, double* Ek);
 
+/* Asynchronous E and eps: enqueue, on the simulation's stream, the E and eps
+ * of the state at that point of the stream (the kin_stats arithmetic, bitwise
+ * the same values) and a copy of them into out[0] (E) and out[1] (eps), and
+ * return without waiting.  out: 2 doubles of host memory that the caller
+ * keeps valid until the copy has completed (kin_sync, or an event recorded on
+ * the stream after this call); page-locked memory keeps the call asynchronous
+ * (a copy into pageable memory waits for the stream).  No check of the values
+ * is made: the caller tests them for finiteness once they have arrived, and
+ * errors reported by the simulation's kernels surface at the next kin_sync.
+ * KIN_EINVAL for out == NULL. */
+int kin_stats_async(kin_sim* sim, double* out);
+
+/* kin_step(sim, n) followed by kin_stats_async(sim, out), with the fused
+ * velocity of kin_step_stats on the last step. */
+int kin_step_stats_async(kin_sim* sim, int n, double* out);
+
 /* Derived statistics of the current state (Sec. III; synchronises the stream):
  *   out[0] E          <u.u>/2
  *   out[1] u'         sqrt(<u.u>/3)

@@ -52,6 +52,14 @@ def _strerror(code: int) -> str:
     return _lib.kin_strerror(code).decode()
 
 
+def _out2(out):
+    """Pointer to a float64 C-contiguous array of at least 2 elements."""
+    if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous
+            and out.size >= 2):
+        raise ValueError("out must be a C-contiguous float64 array of at least 2 elements")
+    return out.ctypes.data_as(ctypes.c_void_p)
+
+
 def _declare(lib):
     c_int, c_double, c_void_p, c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
     c_i64, c_u64 = ctypes.c_int64, ctypes.c_uint64
@@ -69,6 +77,8 @@ def _declare(lib):
         "kin_step": (c_int, [P, c_int]),
         "kin_stats": (c_int, [P, P, P, P]),
         "kin_step_stats": (c_int, [P, c_int, P, P, P]),
+        "kin_stats_async": (c_int, [P, P]),
+        "kin_step_stats_async": (c_int, [P, c_int, P]),
         "kin_init_consistent": (c_int, [P, c_int, ctypes.c_double, P, P]),
         "kin_derived_stats": (c_int, [P, P, P]),
         "kin_num_shells": (c_int, [c_int]),
@@ -282,6 +292,17 @@ class Sim:
         if spectrum:
             return float(E[0]), float(eps[0]), Ek
         return float(E[0]), float(eps[0])
+
+    def stats_async(self, out: np.ndarray):
+        """kin_stats_async: enqueue (E, eps) of the current state into out[0:2]
+        (float64, C-contiguous; page-locked memory, e.g. a pinned torch tensor's
+        numpy view, keeps the call asynchronous) and return at once; the values
+        are there once the stream has passed this point."""
+        _check(lib().kin_stats_async(self._h, _out2(out)), "kin_stats_async")
+
+    def step_stats_async(self, n: int, out: np.ndarray):
+        """kin_step_stats_async: n steps, then stats_async(out) of the new state."""
+        _check(lib().kin_step_stats_async(self._h, int(n), _out2(out)), "kin_step_stats_async")
 
     DERIVED = ("E", "uprime", "eps", "lambda", "Re_lambda", "eta", "S", "F")
 

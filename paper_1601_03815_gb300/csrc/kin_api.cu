@@ -232,6 +232,30 @@ int launch_step(kin_sim* s, float* uvel = nullptr) {
     return KIN_OK;
 }
 
+// Enqueue E and eps of the current state into red_out[0..1] (device).
+int enqueue_energy_dissipation(kin_sim* s) {
+    if (int r = ensure_u(s)) return r;
+    if (s->storage == ST_F64) {
+        CK(velocity_field(s->storage, s->buf[s->cur], shifted(s), s->N, s->u, s->stream));
+        CK(energy_dissipation(s->u, s->N, s->nu, s->red, s->red_out, s->stream));
+        s->launches += 3;
+    } else {
+        // FP32 arithmetic per cell (FP64 on this GPU runs at a small fraction
+        // of the FP32 rate), FP64 sums; the velocity pass is skipped when u32
+        // already holds this state's velocity (left by the step that made it,
+        // or by an earlier call)
+        if (!s->u32) CK(cudaMalloc(&s->u32, sizeof(float) * 3 * ncell(s)));
+        if (s->u32_epoch != s->epoch) {
+            CK(velocity_field32(s->storage, s->buf[s->cur], shifted(s), s->N, s->u32, s->stream));
+            s->launches += 1;
+            s->u32_epoch = s->epoch;
+        }
+        CK(energy_dissipation32(s->u32, s->N, s->nu, s->red, s->red_out, s->stream));
+        s->launches += 2;
+    }
+    return KIN_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -519,6 +543,29 @@ int kin_step_stats(kin_sim* s, int n, double* E, double* eps, double* Ek) {
     return kin_stats(s, E, eps, Ek);
 }
 
+int kin_stats_async(kin_sim* s, double* out) {
+    NvtxRange nvtx_("kin_stats_async");
+    if (int r = usable(s)) return r;
+    if (!out) return fail(KIN_EINVAL, "NULL output");
+    DeviceGuard g(s->device);
+    if (int r = enqueue_energy_dissipation(s)) return r;
+    CK(cudaMemcpyAsync(out, s->red_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    return KIN_OK;
+}
+
+int kin_step_stats_async(kin_sim* s, int n, double* out) {
+    NvtxRange nvtx_("kin_step_stats_async");
+    if (int r = usable(s)) return r;
+    if (n < 0) return fail(KIN_EINVAL, "negative step count");
+    if (!out) return fail(KIN_EINVAL, "NULL output");
+    DeviceGuard g(s->device);
+    const bool fuse = n > 0 && fused_velocity_ok(s);
+    if (fuse && !s->u32) CK(cudaMalloc(&s->u32, sizeof(float) * 3 * ncell(s)));
+    for (int k = 0; k < n; ++k)
+        if (int r = launch_step(s, fuse && k == n - 1 ? s->u32 : nullptr)) return r;
+    return kin_stats_async(s, out);
+}
+
 int kin_init_consistent(kin_sim* s, int max_iter, double tol, int* iters, double* residual) {
     NvtxRange nvtx_("kin_init_consistent");
     if (int r = usable(s)) return r;
@@ -575,25 +622,7 @@ int kin_stats(kin_sim* s, double* E, double* eps, double* Ek) {
     NvtxRange nvtx_("kin_stats");
     if (int r = usable(s)) return r;
     DeviceGuard g(s->device);
-    if (int r = ensure_u(s)) return r;
-    if (s->storage == ST_F64) {
-        CK(velocity_field(s->storage, s->buf[s->cur], shifted(s), s->N, s->u, s->stream));
-        CK(energy_dissipation(s->u, s->N, s->nu, s->red, s->red_out, s->stream));
-        s->launches += 3;
-    } else {
-        // FP32 arithmetic per cell (FP64 on this GPU runs at a small fraction
-        // of the FP32 rate), FP64 sums; the velocity pass is skipped when u32
-        // already holds this state's velocity (left by the step that made it,
-        // or by an earlier call)
-        if (!s->u32) CK(cudaMalloc(&s->u32, sizeof(float) * 3 * ncell(s)));
-        if (s->u32_epoch != s->epoch) {
-            CK(velocity_field32(s->storage, s->buf[s->cur], shifted(s), s->N, s->u32, s->stream));
-            s->launches += 1;
-            s->u32_epoch = s->epoch;
-        }
-        CK(energy_dissipation32(s->u32, s->N, s->nu, s->red, s->red_out, s->stream));
-        s->launches += 2;
-    }
+    if (int r = enqueue_energy_dissipation(s)) return r;
     // E, eps and the step kernels' error flag in one synchronisation
     CK(cudaMemcpyAsync(s->h_pin, s->red_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaMemcpyAsync(s->h_pin + 2, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));

@@ -83,6 +83,9 @@ def test_invalid_arguments_are_rejected_without_a_device(libkin):
     assert libkin.kin_step(None, 1) == -1
     assert libkin.kin_step_stats(None, 1, ctypes.byref(d), ctypes.byref(d), None) == -1
     assert libkin.kin_init_consistent(None, 10, ctypes.c_double(0.0), None, None) == -1
+    out = (ctypes.c_double * 2)()
+    assert libkin.kin_stats_async(None, out) == -1
+    assert libkin.kin_step_stats_async(None, 1, out) == -1
     libkin.kin_destroy(None)  # NULL-safe
 
 

@@ -91,3 +91,47 @@ def test_cached_velocity_follows_the_state(kin, orc):
     assert a.stats() == b.stats()
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("scheme", ["lbe", "dugks"])
+@pytest.mark.parametrize("storage", [0, 1, 3])
+def test_async_statistics_equal_the_synchronous_ones(kin, orc, scheme, storage):
+    """kin_stats_async and kin_step_stats_async deliver the kin_stats /
+    kin_step_stats values bit for bit into page-locked host memory, also when
+    a loop keeps several steps in flight and reads each result one step late
+    (events recorded on the simulation's stream)."""
+    import torch
+
+    N, steps = 36, 6
+    f0 = _state(orc, N, 700)
+    dt = 1.0 if scheme == "lbe" else 0.5
+    code = kin.LBE_MRT if scheme == "lbe" else kin.DUGKS
+    stream = torch.cuda.Stream()
+    a = kin.Sim(N, code, 0.011, 0.1, dt, storage, stream=stream)
+    b = kin.Sim(N, code, 0.011, 0.1, dt, storage)
+    a.set_f(f0)
+    b.set_f(f0)
+    out = torch.zeros((steps + 1, 2), dtype=torch.float64, pin_memory=True).numpy()
+    a.stats_async(out[0])
+    events = []
+    for k in range(1, steps + 1):
+        if k % 2:
+            a.step_stats_async(1, out[k])
+        else:
+            a.step(1)
+            a.stats_async(out[k])
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        events.append(ev)
+        if k > 1:
+            events[k - 2].synchronize()
+            assert np.all(np.isfinite(out[k - 1]))
+    a.sync()
+    want = [b.stats()]
+    for k in range(1, steps + 1):
+        want.append(b.step_stats(1))
+    np.testing.assert_array_equal(out, np.array(want))
+    with pytest.raises(ValueError):
+        a.stats_async(np.zeros(1))
+    a.close()
+    b.close()
