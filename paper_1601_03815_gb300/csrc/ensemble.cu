@@ -157,9 +157,9 @@ __global__ void __launch_bounds__(32 * (TY + 2), 1) ensemble_kernel(KIN_ENSEMBLE
     ensemble_body<TY, WIDE>(mem, items, nitems, nsteps, done, next_item, status, wait_cycles, stall_test);
 }
 
-// 6-row tiles, the form that leaves room for LBE blocks: held to 160 registers
-// a thread (152 used), since 8 warps at the compiler's free choice (214) would
-// leave room for one LBE warp a scheduler instead of three.
+// 6-row tiles, the form beside which LBE blocks run: held to 160 registers a
+// thread (152 used; at the compiler's free choice it takes 214), so that the
+// 8-warp block leaves most of the SM's registers to the LBE blocks.
 template <bool WIDE>
 __global__ void __maxnreg__(160) ensemble_kernel6(KIN_ENSEMBLE_PARAMS) {
     ensemble_body<6, WIDE>(mem, items, nitems, nsteps, done, next_item, status, wait_cycles, stall_test);
@@ -550,13 +550,10 @@ int kin_ensemble_create(kin_sim* const* members, int n, kin_ensemble** out) {
             e->lbe_ids.push_back(m);
         }
     }
-    // LBE blocks run beside a DUGKS block only if the registers allow it, and
-    // a block occupies registers as if it had ceil(warps / 4) warps on each of
-    // the SM's four schedulers (measured: with 8-row tiles, a 10-warp block
-    // of 158 registers a thread, no LBE block of any size ran beside it; with
-    // 4-row tiles, 6 warps, they did).  A 10-warp block then leaves 1,024
-    // registers a scheduler, less than one LBE warp's 1,792; an 8-warp block
-    // (6-row tiles) leaves 6,144, room for three 4-warp LBE blocks.
+    // Measured: LBE blocks of any size ran beside 6- and 8-warp DUGKS blocks
+    // (4- and 6-row tiles) and never beside the 10-warp blocks of 8-row tiles,
+    // even with those held to 152 registers a thread; so when both schemes
+    // are present the DUGKS tiles have 6 rows.
     if (!e->dugks_ids.empty() && !e->lbe_ids.empty()) e->tile_y = 6;
     e->device = dev;
     int prev = 0;
