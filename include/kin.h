@@ -20,9 +20,10 @@
  *
  * Every int-returning call returns KIN_OK (0) or a negative KIN_E* code;
  * kin_strerror() names the code and kin_last_error() describes the last
- * failure on the calling thread.  No call retains a host pointer.  All device
- * work is ordered on the simulation's stream; calls that return host data
- * synchronise that stream first.
+ * failure on the calling thread.  No call retains a host pointer beyond the
+ * stream work it enqueues.  All device work is ordered on the simulation's
+ * stream; calls that return host data synchronise that stream first, except
+ * kin_stats_async / kin_step_stats_async, which enqueue their copy.
  */
 #ifndef KIN_H
 #define KIN_H
