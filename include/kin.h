@@ -243,11 +243,11 @@ int kin_num_shells(int N);
  *            (default: when a plane's tile columns fill fewer than 1.5
  *            waves of blocks, the length with the shortest list schedule of
  *            the grid; otherwise about two waves of blocks)
- *   variant  DUGKS: 0 = fused single launch, f-tilde staged by per-thread
- *            cp.async copies two planes ahead (default); 1 = two launches
- *            (pre-step into scratch, then flux + update)
- * Results do not depend on the launch shape or variant beyond rounding
- * order (the fused and two-launch forms sum the same terms differently).
+ *   variant  DUGKS: 0 = fused single launch, f-tilde staged in shared
+ *            memory by cp.async copies two planes ahead (default); 1 = two
+ *            launches (pre-step into scratch, then flux + update)
+ * The fused step's results do not depend on tile_y or zchunk (bitwise); the
+ * two-launch form sums the same terms in another order (rounding only).
  * Other variant values return KIN_EINVAL. */
 int kin_set_tuning(kin_sim* sim, int block_x, int tile_y, int zchunk, int variant);
 
