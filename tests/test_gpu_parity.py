@@ -325,3 +325,24 @@ def test_lbe_block_sizes_above_the_launch_bounds(kin, storage):
             sim.step(2)
             np.testing.assert_array_equal(sim.sample_f(list(range(0, N ** 3, 9973))), want)
             sim.close()
+
+
+@pytest.mark.parametrize("storage", [0, 1, 3])
+def test_fused_dugks_results_do_not_depend_on_the_tile_shape(kin, orc, storage):
+    """The fused DUGKS step gives the same bits for every tile height and z
+    chunk (a cell's arithmetic does not depend on which tile or plane range
+    computes it); N = 38 makes every shape ragged."""
+    N = 38
+    f0 = _state(orc, N, 4242)
+    outs = []
+    for ty, zc in ((8, 0), (4, 3), (8, 7), (4, 38)):
+        if storage == 3 and ty == 8:
+            continue  # FP64 storage always runs 4-row tiles
+        sim = kin.Sim(N, kin.DUGKS, 0.013, 0.1, 0.5, storage)
+        sim.set_tuning(tile_y=ty, zchunk=zc if zc else 0)
+        sim.set_f(f0)
+        sim.step(3)
+        outs.append(sim.get_f())
+        sim.close()
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
