@@ -3,7 +3,7 @@
 isotropic turbulence" (arXiv:1601.03815).
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
-CPU-baseline leg of ``bench.py`` may import this package.  The product library
+CPU-baseline and reference legs of ``bench.py`` may import this package.  The product library
 (``paper_1601_03815_gb300``) never imports it, and it never imports the product.
 
 The time steppers live in ``kin_oracle.c`` (plain C, FP64, OpenMP); this module
